@@ -176,6 +176,7 @@ void or_grid_policy(int64_t n, const float* xyf, int k, int n_int_min, int grid_
     double L = (double)hi - (double)lo;
     if (L < OR_L_FLOOR) L = OR_L_FLOOR;
     double c = ceil(L);
+    if (c > 2.0e9) c = 2.0e9; /* keeps the integer conversion defined */
     int n_int = (c > (double)n_int_min) ? (int)c : n_int_min;
     int cap = grid_max / k;
     if (n_int > cap) n_int = cap;
@@ -206,10 +207,9 @@ void or_grid_policy(int64_t n, const float* xyf, int k, int n_int_min, int grid_
 int or_box_f32(float x, float lo, float h, int n_int) {
     volatile float d = x - lo;
     volatile float t = d / h;
-    int a = (int)floorf(t);
-    if (a < 0) a = 0;
-    if (a > n_int - 1) a = n_int - 1;
-    return a;
+    float a = floorf(t);
+    /* NaN and negative quotients go to box 0, quotients past the end to the last box */
+    return (a >= 0.0f) ? ((a <= (float)(n_int - 1)) ? (int)a : n_int - 1) : 0;
 }
 
 /* Lagrange basis over the k equispaced nodes t_l = (l + 1/2) / k of a unit box,
