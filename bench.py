@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Throughput of one t-FDP iteration (arXiv 2303.03964) on one GB300.
+
+A step is one full iteration of the hot path -- bin/sort, spread, grid interaction by
+FFT, back-projection, attraction over the edge list, position update -- on a seeded
+synthetic graph with its inputs resident in HBM. The default workload is the
+1000 x 1000 lattice (1M nodes, 1,998,000 edges) with uniform initial positions,
+ibFFT repulsion with k = 3 and a grid of at most 1023^2 nodes (FFT size 2048).
+
+Prints one JSON line. Timing: W warm-up steps, then K steps each preceded by an L2
+flush (a 256 MiB write) and timed with CUDA events on the library's stream; per-stage
+CUDA events captured inside the iteration graph give the dominant kernel's live
+duration for the roofline. `e2e` repeats the steps through the C ABI with host
+buffers (positions in and out of pinned host memory every step, wall clock).
+
+--impl reference times the FP64 CPU oracle on the same workload (the reference arm).
+Multi-GPU (torchrun): every rank lays out its own copy of the graph (replicas; one
+graph does not shard without a collective, which this path does not have).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-iterations/s at 1M nodes (mixed vs plain FP32, same force error); p50/p99 update"
+UNIT = "node-iterations/s"
+FLUSH_BYTES = 256 << 20
+
+WORKLOADS = {
+    "lattice_1m": {"desc": "1000x1000 lattice, n=1,000,000, m=1,998,000, U[-500,500]^2",
+                   "rep": "fft", "k": 3, "grid_max": 1023, "total_iters": 300},
+    "ba_2m": {"desc": "Barabasi-Albert n=2,000,000, m0=3, U[-707,707]^2",
+              "rep": "fft", "k": 3, "grid_max": 1023, "total_iters": 300},
+    "sbm_100k": {"desc": "SBM n=100,000, 20 blocks, mean degree 10, 90% intra, U[-50,50]^2",
+                 "rep": "fft", "k": 3, "grid_max": 255, "total_iters": 500},
+    "er_2000_exact": {"desc": "ER n=2000, m=8000, U[-50,50]^2, exact repulsion",
+                      "rep": "exact", "k": 3, "grid_max": 255, "total_iters": 100},
+}
+
+# DRAM bytes of the dominant kernel from one ncu capture, per launch, keyed by stage,
+# valid only while the kernel source is unchanged (sha256 of the file that defines it).
+NCU_TRAFFIC = {}
+
+
+def make_workload(name):
+    from paper_2303_03964_gb300 import synth
+    if name == "lattice_1m":
+        e, xy = synth.lattice_1m()
+    elif name == "ba_2m":
+        e, xy = synth.ba_2m()
+    elif name == "sbm_100k":
+        e, xy = synth.sbm_100k()
+    elif name == "er_2000_exact":
+        e, xy = synth.er_2000()
+    else:
+        raise KeyError(name)
+    return e, xy
+
+
+def stage_bytes(stage, n, m, G, P, nbox):
+    """Algorithmic bytes of one launch of a stage: each input read once, each output
+    written once (FP32 positions 8 B/node, int32 indices 4 B)."""
+    NH = P // 2 + 1
+    if stage == "sort":
+        # bin: read xy, write (key, slot); scan: cnt -> off; scatter: read (key, slot),
+        # xy, write sorted xy + perm
+        return 8 * n + 8 * n + 2 * 4 * nbox + (8 * n + 8 * n) + (8 * n + 4 * n)
+    if stage == "spread":
+        return 8 * n + 4 * nbox + 3 * 4 * G * G
+    if stage == "rows_fwd":
+        return 3 * 4 * G * G + 3 * 8 * G * NH
+    if stage == "cols":
+        return 3 * 8 * G * NH + 3 * 4 * P * NH + 3 * 8 * G * NH
+    if stage == "rows_inv":
+        return 3 * 8 * G * NH + 16 * G * G
+    if stage == "gather_update":
+        # xy in, grid (A, O^x, O^y) once, rowptr, col, neighbour positions, xy out
+        return 8 * n + 16 * G * G + 4 * (n + 1) + 4 * 2 * m + 8 * 2 * m + 8 * n
+    if stage == "edge_update":
+        return 8 * n + 4 * (n + 1) + 4 * 2 * m + 8 * 2 * m + 8 * n
+    return 0
+
+
+def stage_source(stage):
+    return {"sort": "node_kernels.cu", "spread": "node_kernels.cu",
+            "gather_update": "node_kernels.cu", "edge_update": "node_kernels.cu",
+            "exact": "node_kernels.cu", "rows_fwd": "fft_kernels.cu", "cols": "fft_kernels.cu",
+            "rows_inv": "fft_kernels.cu", "spectrum": "fft_kernels.cu"}.get(stage)
+
+
+def source_sha(stage):
+    src = stage_source(stage)
+    if not src:
+        return None
+    path = os.path.join(ROOT, "paper_2303_03964_gb300", "csrc", src)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(e, xy, spec, budget_s=15.0):
+    """The FP64 oracle as it stands, on the same workload, on this host's cores."""
+    import numpy as np
+    import oracle
+    x = xy.astype(np.float64)
+    mode = "exact" if spec["rep"] == "exact" else "fft"
+    iters = 0
+    t0 = time.perf_counter()
+    while True:
+        x = oracle.iterate(x, e, 1, mode=mode, k=spec["k"], grid_max=spec["grid_max"],
+                           T=spec["total_iters"], t0=iters)
+        iters += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or iters >= 50:
+            break
+    n = xy.shape[0]
+    return {"value": n * iters / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "%d full iteration(s) of the same workload (%s repulsion), %.1f s" % (
+                iters, mode, el)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]
+    e, xy = make_workload(args.workload)
+    import numpy as np
+    import oracle
+    x = xy.astype(np.float64)
+    mode = "exact" if spec["rep"] == "exact" else "fft"
+    for w in range(args.warmup):
+        x = oracle.iterate(x, e, 1, mode=mode, k=spec["k"], grid_max=spec["grid_max"],
+                           T=spec["total_iters"], t0=w)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        x = oracle.iterate(x, e, 1, mode=mode, k=spec["k"], grid_max=spec["grid_max"],
+                           T=spec["total_iters"], t0=args.warmup + s)
+        times.append(time.perf_counter() - t0)
+    n = xy.shape[0]
+    tot = sum(times)
+    value = n * len(times) / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "rep": mode,
+                       "k": spec["k"], "grid_max": spec["grid_max"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": "one full FP64 oracle iteration per step on the same workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2303_03964_gb300 import tfdp
+
+    spec = WORKLOADS[args.workload]
+    e, xy = make_workload(args.workload)
+    n, m = xy.shape[0], e.shape[0]
+    rep = tfdp.REP_EXACT if spec["rep"] == "exact" else tfdp.REP_FFT
+    params = tfdp.params_default(rep_mode=rep, k_interp=spec["k"], grid_max=spec["grid_max"],
+                                 total_iters=spec["total_iters"])
+    stream = torch.cuda.Stream()
+    g = tfdp.Graph(n, e, xy, params, stream=stream.cuda_stream)
+    g.set_stage_timing(True)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        g.iterate(1)
+        ev1.record(stream)
+        stream.synchronize()
+        return ev0.elapsed_time(ev1), g.stage_times()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, stages = [], []
+    for _ in range(args.steps):
+        ms, st = step()
+        step_ms.append(ms)
+        stages.append(st)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        total_ms = float(t.item())
+    stats = g.stats()
+
+    # end to end through the C ABI with host buffers: pinned positions in and out
+    host_in = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+    host_out = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+    g.get_positions(host_out.numpy())
+    host_in.copy_(host_out)
+    e2e_s = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        g.set_positions(host_in.numpy())
+        g.iterate(1)
+        g.get_positions(host_out.numpy())
+        e2e_s.append(time.perf_counter() - t0)
+        host_in.copy_(host_out)
+    e2e_total = sum(e2e_s)
+    if ws > 1:
+        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_total = float(t.item())
+
+    if rank != 0:
+        g.close()
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    mean_stage = {k: statistics.fmean(s[k] for s in stages) for k in stages[0]}
+    G, P = stats["grid_G"], stats["fft_P"]
+    nbox = stats["grid_n_int"] ** 2
+    cand = {k: v for k, v in mean_stage.items() if v > 0 and k != "spectrum"}
+    dom = max(cand, key=cand.get)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if dom == "exact":
+        flops = 11.0 * n * n
+        roof = {"stage": dom, "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
+    else:
+        bytes_ = stage_bytes(dom, n, m, G, P, nbox)
+        ach = bytes_ / (mean_stage[dom] * 1e-3) / 1e9
+        tr = NCU_TRAFFIC.get((args.workload, dom))
+        traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(dom) else None
+        roof = {"stage": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": bytes_,
+                "peak_kind": peak_kind + " hbm_gbs (burst copy)"}
+    cpu = None
+    if not args.no_cpu_baseline and ws >= 1 and rank == 0:
+        cpu = cpu_baseline(e, xy, spec)
+    value = ws * n * args.steps / (total_ms * 1e-3)
+    q = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "rep": spec["rep"],
+                   "k": spec["k"], "grid_max": spec["grid_max"], "grid_G": G, "fft_P": P,
+                   "grid_policy": "SNAP_H", "precision": "fp32",
+                   "l2": "flushed before every step (256 MiB write, outside the timed events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "step_ms_p50": q[len(q) // 2], "step_ms_p99": q[min(len(q) - 1, int(0.99 * len(q)))],
+        "mixed": None,
+        "stages_ms": mean_stage,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * n * args.steps / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": stats["kernels_per_iteration"] * args.steps,
+        "clocks": clocks,
+        "device_flags": stats["device_flags"],
+    }
+    print(json.dumps(line), flush=True)
+    g.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lattice_1m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,222 @@
+/*
+ * tfdp.h -- C ABI of the GB300 (sm_103a) t-FDP force-evaluation library.
+ *
+ * t-FDP is the force-directed graph layout of "Force-directed graph layouts
+ * revisited: a new force based on the t-Distribution" (Zhong et al., arXiv
+ * 2303.03964). One iteration computes, for every node i of an undirected graph
+ * with n nodes and m edges:
+ *
+ *   frep(i) = sum_{j != i} (x_i - x_j) / (1 + |x_i - x_j|^2)^gamma
+ *             repulsive t-force, Sec. 3.3 Eq. (replusive), Sec. 3.4 Eq. (repfK);
+ *             exact O(n^2) sum, or the interpolation-based FFT ("ibFFT") of Sec. 3.4
+ *   fatt(i) = alpha * sum_{j <-> i} (1 + beta / (1 + |x_i - x_j|^2)) (x_j - x_i)
+ *             attractive force, Sec. 3.3 Eq. (newforce), weighted by alpha as in
+ *             the resultant force of Sec. 3.3
+ *   x_i    += D(i) * min(1, s_t / |D(i)|),   D(i) = frep(i) + fatt(i)
+ *             position update (Sec. 3.1: the resultant force moves each node until
+ *             convergence). The step s_t = s0 (s_min / s0)^(t / (T - 1)) is a reading:
+ *             the paper gives no schedule.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a tfdp_status; no C++ exception crosses the ABI.
+ *   - Arrays of positions or forces are n x 2 row-major FP32 (x0, y0, x1, y1, ...),
+ *     in the caller's node order.
+ *   - Pointers flagged `on_device` are CUDA device pointers on the graph's device,
+ *     otherwise host pointers. Input buffers are copied; the caller keeps ownership
+ *     of every buffer it passes and may free it when the call returns (for async
+ *     calls: once the call returns, host inputs have been consumed).
+ *   - A graph owns its device memory; tfdp_destroy_graph frees it.
+ *   - Calls on one graph are not thread-safe; different graphs are independent.
+ *   - Work is enqueued on the CUDA stream given at creation (0 = legacy default).
+ */
+#ifndef TFDP_H
+#define TFDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TFDP_OK = 0,
+    TFDP_ERR_INVALID_ARG = 1,   /* null pointer, negative size, unknown enum value */
+    TFDP_ERR_BAD_GRAPH = 2,     /* edge id out of range, self-loop or duplicate edge */
+    TFDP_ERR_PARAM_RANGE = 3,   /* gamma <= 1, alpha < 0, beta < 0, bad k or grid cap */
+    TFDP_ERR_OUT_OF_MEMORY = 4, /* device or host allocation refused */
+    TFDP_ERR_CUDA = 5,          /* a CUDA runtime call failed (see tfdp_last_cuda_error) */
+    TFDP_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    TFDP_ERR_BUSY = 7,          /* the object is in use by another request */
+    TFDP_ERR_DEVICE_CHECK = 8   /* a device-side consistency check failed */
+} tfdp_status;
+
+/* How the repulsive sum is evaluated. */
+typedef enum {
+    TFDP_REP_EXACT = 0, /* tiled all-pairs sum of Eq. (repfK), Sec. 3.4 "exact method" */
+    TFDP_REP_FFT = 1    /* interpolation-based FFT of Sec. 3.4 */
+} tfdp_rep_mode;
+
+/* Arithmetic of the grid convolution (the FFT step of Sec. 3.4). */
+typedef enum {
+    TFDP_PREC_FP32 = 0,  /* FP32 spread, FFT and interpolation */
+    TFDP_PREC_BF16X3 = 1 /* reserved: BF16 split-precision tensor-core convolution */
+} tfdp_precision;
+
+/* Box side of the interpolation grid, Sec. 3.4 ("Choices of k"). Both policies take
+ * the layout square [x_min, x_max]^2 (x_min / x_max = min / max over both
+ * coordinates), N_int = min(max(n_int_min, ceil(L)), floor(grid_max / k)) with
+ * L = x_max - x_min, and G = N_int * k grid nodes per axis.                       */
+typedef enum {
+    TFDP_GRID_PAPER = 0, /* h = L / N_int: recomputed, and the spectrum rebuilt, every iteration */
+    TFDP_GRID_SNAP_H = 1 /* h = smallest 2^e (16 + j) / 16 >= L / N_int: the spectrum is
+                            rebuilt only when h crosses a 1/16-octave step */
+} tfdp_grid_policy;
+
+typedef struct {
+    double alpha;        /* attraction weight (Sec. 3.3), default 0.1, >= 0 */
+    double beta;         /* short-range attraction weight (Sec. 3.3), default 8, >= 0 */
+    double gamma;        /* repulsion exponent (Sec. 3.3), default 2, > 1 (Eq. exponentcondiction) */
+    int32_t k_interp;    /* interpolation nodes per box and axis, 1..3, default 3 (Sec. 3.4) */
+    int32_t n_int_min;   /* lower bound of N_int, default 50 (Sec. 3.4) */
+    int32_t grid_max;    /* cap on G = N_int * k, default 1023; sizes the FFT: P = nextpow2(2 grid_max - 1) */
+    int32_t grid_policy; /* tfdp_grid_policy, default TFDP_GRID_SNAP_H */
+    int32_t rep_mode;    /* tfdp_rep_mode, default TFDP_REP_FFT */
+    int32_t precision;   /* tfdp_precision, default TFDP_PREC_FP32 */
+    double step0;        /* s0, default 1.0 (layout units) */
+    double step_min;     /* s_min, default 0.01 */
+    int32_t total_iters; /* T of the step schedule, default 300 (Sec. 4.1 implies 300) */
+    int32_t reserved[7]; /* must be zero */
+} tfdp_params;
+
+/* Per-graph diagnostics of the last completed iteration (synchronises the stream). */
+typedef struct {
+    int64_t iteration;        /* number of iterations done (next t) */
+    double net_frep[2];       /* FP64 sum over nodes of frep(i); ~0 by antisymmetry */
+    double grid_lo;           /* origin of the grid square */
+    double grid_h;            /* box side */
+    int32_t grid_n_int;       /* boxes per axis */
+    int32_t grid_G;           /* grid nodes per axis */
+    int32_t fft_P;            /* FFT size per axis */
+    int32_t spectrum_builds;  /* how many times the kernel spectrum was (re)built */
+    int32_t device_flags;     /* nonzero: a device-side check failed (bit field) */
+    int32_t kernels_per_iteration; /* kernel launches of one iteration in the current mode */
+    int32_t reserved[6];
+} tfdp_stats;
+
+/* Stages of one iteration, in launch order, for tfdp_get_stage_times. */
+enum {
+    TFDP_STAGE_SORT = 0,          /* FFT path: box of each node, counting sort (5 kernels) */
+    TFDP_STAGE_SPREAD = 1,        /* FFT path: Lagrange projection onto the grid */
+    TFDP_STAGE_SPECTRUM = 2,      /* FFT path: kernel spectrum (returns at once when cached) */
+    TFDP_STAGE_ROWS_FWD = 3,      /* FFT path: forward transform along x */
+    TFDP_STAGE_COLS = 4,          /* FFT path: transform along y, spectral product, inverse */
+    TFDP_STAGE_ROWS_INV = 5,      /* FFT path: inverse transform along x */
+    TFDP_STAGE_GATHER_UPDATE = 6, /* FFT path: back-projection + attraction + update */
+    TFDP_STAGE_EXACT = 7,         /* exact path: all-pairs repulsion */
+    TFDP_STAGE_EDGE_UPDATE = 8,   /* exact path: attraction + update */
+    TFDP_NUM_STAGES = 9
+};
+
+typedef struct tfdp_graph tfdp_graph;
+
+/* Human-readable name of a status code (static storage). */
+const char* tfdp_status_str(tfdp_status s);
+
+/* Message of the last CUDA error seen by this thread's calls ("" if none). */
+const char* tfdp_last_cuda_error(void);
+
+/* Fill *out with the defaults: alpha 0.1, beta 8, gamma 2 (Sec. 3.3), k 3,
+ * n_int_min 50 (Sec. 3.4), grid_max 1023, SNAP_H, FFT repulsion, FP32, s0 1,
+ * s_min 0.01, T 300. */
+tfdp_status tfdp_params_default(tfdp_params* out);
+
+/* Check a parameter set against Sec. 3.3: gamma > 1 (Eq. exponentcondiction),
+ * alpha >= 0, beta >= 0, 1 <= k <= 3, grid_max >= k, step0 >= step_min > 0,
+ * total_iters >= 1. *weight_ok (may be NULL) is set to 1 iff alpha (1 + beta) < 1
+ * (Eq. limitweight); a set that breaks only that soft condition is accepted. */
+tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok);
+
+/*
+ * Create a graph: n nodes, m undirected edges.
+ *   edges   host, 2m int32 node ids (i0, j0, i1, j1, ...); copied. An id outside
+ *           [0, n), a self-loop or a duplicate pair (in either order) gives
+ *           TFDP_ERR_BAD_GRAPH. m = 0 is allowed (edges may then be NULL).
+ *   xy0     host, n x 2 FP32 initial positions; copied. NULL: positions uniform in
+ *           [-sqrt(n)/2, sqrt(n)/2]^2 from `seed` (SplitMix64 counter generator).
+ *   params  NULL = defaults. grid_max and k_interp size the device buffers.
+ *   stream  cudaStream_t to enqueue on (NULL = legacy default stream).
+ *   out     receives the handle; untouched on error.
+ * Allocates all device memory of the graph (positions, CSR, sort buffers, grids,
+ * spectra) on the current device. n = 0 is allowed.
+ */
+tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const float* xy0,
+                              uint64_t seed, const tfdp_params* params, void* stream,
+                              tfdp_graph** out);
+
+/* Replace the parameters. Changing gamma, k_interp, grid policy or grid_max marks
+ * the kernel spectrum stale (alpha and beta only enter the edge term, Sec. 3.3, and
+ * never need it). A larger grid_max or k reallocates the grid buffers. Does not
+ * reset the iteration counter. */
+tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p);
+tfdp_status tfdp_get_params(const tfdp_graph* g, tfdp_params* out);
+
+/* Overwrite all positions (n x 2 FP32, caller order). Asynchronous on the stream. */
+tfdp_status tfdp_set_positions(tfdp_graph* g, const float* xy, int on_device);
+
+/* Copy positions (n x 2 FP32, caller order) out. Synchronises the stream. */
+tfdp_status tfdp_get_positions(tfdp_graph* g, float* xy, int on_device);
+
+/* Run `iters` >= 0 iterations, starting at the graph's iteration counter t (which
+ * selects s_t); advances t by iters. Asynchronous: launches one captured CUDA graph
+ * per iteration on the stream. Errors of earlier asynchronous work surface here or
+ * in the next synchronising call. */
+tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters);
+
+/* Set / read the iteration counter t (warm restart, Sec. 5 "Global Refinement"). */
+tfdp_status tfdp_set_iteration(tfdp_graph* g, int64_t t);
+
+/* Evaluate frep and fatt (n x 2 FP32 each, caller order; either may be NULL) at
+ * the current positions without moving any node. Synchronises the stream. */
+tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_device);
+
+/* Diagnostics of the last iteration or force evaluation. Synchronises the stream. */
+tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out);
+
+/* Record CUDA events between the stages of every iteration (enable = 1) or not (0).
+ * Changing it recaptures the iteration graphs at the next tfdp_iterate. */
+tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable);
+
+/* Device time in ms of each stage of the most recent iteration or force evaluation
+ * run with stage timing on; ms has nstages entries indexed by TFDP_STAGE_*, unused
+ * stages are 0. Synchronises the stream. TFDP_ERR_INVALID_ARG if timing is off. */
+tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages);
+
+/* Wait for all work queued on the graph's stream. */
+tfdp_status tfdp_synchronize(tfdp_graph* g);
+
+/* Free the graph and its device memory (synchronises first). NULL is a no-op. */
+tfdp_status tfdp_destroy_graph(tfdp_graph* g);
+
+/*
+ * Test hook: copy an internal buffer of the last FFT-mode force evaluation to host
+ * memory `dst` of `bytes` bytes (TFDP_ERR_INVALID_ARG if too small or unknown).
+ *   TFDP_DEBUG_GRID_CHARGES  3 x G x G FP32: rho, m_x, m_y (the spread, Sec. 3.4 step 1)
+ *   TFDP_DEBUG_GRID_OUTPUT   G x G x 4 FP32: A, O_x, O_y, 0 (the grid interaction, step 2)
+ *   TFDP_DEBUG_SORT_PERM     n int32: node id at each cell-sorted slot
+ *   TFDP_DEBUG_CELL_START    N_int^2 + 1 int32: first sorted slot of each box
+ * Synchronises the stream.
+ */
+enum {
+    TFDP_DEBUG_GRID_CHARGES = 1,
+    TFDP_DEBUG_GRID_OUTPUT = 2,
+    TFDP_DEBUG_SORT_PERM = 3,
+    TFDP_DEBUG_CELL_START = 4
+};
+tfdp_status tfdp_debug_fetch(tfdp_graph* g, int what, void* dst, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TFDP_H */

@@ -1,0 +1,83 @@
+// launch.h -- host-side launch interface between the C ABI (tfdp_api.cu) and the
+// kernel translation units. Plain structs of device pointers and sizes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tfdp {
+
+// Buffers and geometry of the FFT stage (fft_kernels.cu).
+struct FftLaunch {
+    int logP;            // FFT size P = 2^logP per axis (7..13)
+    int G_max;           // largest grid G this graph may use
+    int Gs;              // row stride (and rows per plane) of gin / gout
+    int ystride;         // column stride of T1 / T2 (multiple of 4, >= G_max)
+    const float* gin;    // 3 planes of Gs x Gs: rho, m^x, m^y
+    float2* T1;          // [3][P/2+1][ystride]
+    float2* T2;          // [3][P/2+1][ystride]
+    float4* gout;        // [Gs][Gs] (A, O^x, O^y, 0)
+    float2* S1;          // [3][P/2+1][P] spectrum build scratch
+    float* specK;        // [P/2+1][P]
+    float* specHx;       // [P/2+1][P]
+    float* specHy;       // [P/2+1][P]
+    const float2* tw;    // [P] twiddles exp(-2 pi i t / P)
+    DevState* st;
+    const DevParams* prm;
+};
+
+cudaError_t launch_spectrum(const FftLaunch& a, cudaStream_t s);   // 2 kernels
+cudaError_t launch_rows_fwd(const FftLaunch& a, cudaStream_t s);   // 1 kernel
+cudaError_t launch_cols(const FftLaunch& a, cudaStream_t s);       // 1 kernel
+cudaError_t launch_rows_inv(const FftLaunch& a, cudaStream_t s);   // 1 kernel
+int fft_rows_per_cta(int logP);
+// Shared-memory attributes of the FFT kernels of size 2^logP (call outside stream capture).
+cudaError_t prepare_fft(int logP);
+
+// Buffers of the node stages (node_kernels.cu).
+struct NodeLaunch {
+    int n;
+    int k;                 // interpolation nodes per box and axis
+    int gamma_int;         // 2, 4, 8 for the fast exact kernel, else 0
+    float2* xy[2];         // ping-pong positions; iteration t reads xy[t & 1]
+    const int* rowptr;     // n + 1
+    const int* col;        // 2m
+    DevState* st;
+    const DevParams* prm;
+    // FFT path
+    int nbox_max;          // (G_max / k)^2
+    int* cnt;              // nbox_max (zero between iterations)
+    int* off;              // nbox_max + 1
+    int* bsum;             // scan block sums
+    int2* keyslot;         // n
+    float2* sxy;           // n, cell-sorted positions
+    int* perm;             // n, node id of each sorted slot
+    float* gin;            // spread output
+    int Gs;
+    const float4* gout;    // grid output
+    // exact path
+    float2* part;          // [nchunks][n] partial repulsion
+    int nchunks;
+    // force evaluation outputs (caller order)
+    float2* frep_out;
+    float2* fatt_out;
+};
+
+// Positions -> bbox slot `slot` of the state (min / max over both coordinates).
+cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s);
+// FFT path, before the grid interaction: bin + scan + scatter (5 kernels), spread (1).
+// advance != 0: this is an iteration (t_cur = iter, iter += 1 at the scan).
+cudaError_t launch_fft_sort(const NodeLaunch& a, int advance, cudaStream_t s);
+cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s);
+// FFT path, after the grid interaction: gather + attraction + update (eval = 0) or
+// gather + attraction written to frep_out / fatt_out (eval = 1). 1 kernel.
+cudaError_t launch_fft_back(const NodeLaunch& a, int eval, cudaStream_t s);
+// Exact path: all-pairs repulsion (1 kernel), then attraction + update (eval = 0)
+// or outputs (eval = 1) (1 kernel).
+cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s);
+cudaError_t launch_edge_update(const NodeLaunch& a, int advance, int eval, cudaStream_t s);
+int scan_items_per_block();
+
+}  // namespace tfdp

@@ -1,0 +1,613 @@
+// node_kernels.cu -- per-node stages of one t-FDP iteration (arXiv 2303.03964).
+//
+//   k_bbox           layout square extremes (Sec. 3.4: [x_min, x_max]^2 over both axes)
+//   k_bin            box of every node (Sec. 3.4: "projecting each data point into the
+//                    corresponding grid square"), counting-sort histogram
+//   k_scan_*         exclusive scan of the box counts
+//   k_scatter        cell-sorted copy of the positions
+//   k_spread         Lagrange projection onto the k x k nodes of each box (Sec. 3.4,
+//                    step 1): rho, m^x, m^y; one thread owns one box, so no atomics
+//   k_gather_update  back-projection (step 3), attraction over the CSR (Eq. newforce),
+//                    capped step (update)
+//   k_exact          tiled all-pairs repulsion (Eq. repfK), FP32
+//   k_edge_update    attraction + update for the exact path
+//
+// Node coordinates relative to their box origin are formed exactly (TwoSum and an
+// FMA-exact product), so that FP32 coordinates of magnitude |x| ~ 10^3 keep the
+// precision of the in-box offset.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace tfdp {
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+constexpr int kNodeThreads = 256;
+
+int scan_items_per_block() { return kScanChunk; }
+
+// ---------------------------------------------------------------- box geometry
+struct AxisGeom {
+    float lo, h_hi, h_lo, hk;  // origin, box side as hi + lo FP32 pair, h / k
+    int n_int;
+};
+
+__device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g, int K) {
+    AxisGeom a;
+    a.lo = g.lo_f;
+    a.h_hi = g.h_f;
+    a.h_lo = (float)(g.h - (double)g.h_f);
+    a.hk = (float)(g.h / (double)K);
+    a.n_int = g.n_int;
+    return a;
+}
+
+// Box index b (the FP32 decision shared with the oracle) and the offset of x from the
+// box origin lo + b h, accurate to a few ulps of h.
+__device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off) {
+    float tq;
+    const int b = box_of(x, a.lo, a.h_hi, a.n_int, &tq);
+    // x - lo = s + e exactly (TwoSum)
+    const float s = __fsub_rn(x, a.lo);
+    const float bb = __fsub_rn(s, x);
+    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-a.lo, bb));
+    // b * h_hi = p + pe exactly
+    const float fb = (float)b;
+    const float p = __fmul_rn(fb, a.h_hi);
+    const float pe = __fmaf_rn(fb, a.h_hi, -p);
+    *off = __fadd_rn(__fsub_rn(s, p), __fsub_rn(__fsub_rn(e, pe), __fmul_rn(fb, a.h_lo)));
+    return b;
+}
+
+// ---------------------------------------------------------------- reductions
+struct BlockAcc {
+    float mn, mx;
+    double fx, fy;
+};
+
+// Reduce (min, max, sum fx, sum fy) over the block; thread 0 publishes with atomics.
+__device__ void block_publish(BlockAcc v, DevState* st, int slot, bool bbox) {
+    __shared__ float s_mn[32], s_mx[32];
+    __shared__ double s_fx[32], s_fy[32];
+    v.mn = warp_min(v.mn);
+    v.mx = warp_max(v.mx);
+    v.fx = warp_sum(v.fx);
+    v.fy = warp_sum(v.fy);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { s_mn[w] = v.mn; s_mx[w] = v.mx; s_fx[w] = v.fx; s_fy[w] = v.fy; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        v.mn = lane < nw ? s_mn[lane] : INFINITY;
+        v.mx = lane < nw ? s_mx[lane] : -INFINITY;
+        v.fx = lane < nw ? s_fx[lane] : 0.0;
+        v.fy = lane < nw ? s_fy[lane] : 0.0;
+        v.mn = warp_min(v.mn);
+        v.mx = warp_max(v.mx);
+        v.fx = warp_sum(v.fx);
+        v.fy = warp_sum(v.fy);
+        if (lane == 0) {
+            if (bbox && v.mn <= v.mx) {
+                atomicMin(&st->bbox[slot][0], f2ord(v.mn));
+                atomicMax(&st->bbox[slot][1], f2ord(v.mx));
+            }
+            atomicAdd(&st->net_frep[0], v.fx);
+            atomicAdd(&st->net_frep[1], v.fy);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- bbox
+__global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict__ xy, int n, DevState* st,
+                                                       int slot) {
+    BlockAcc v{INFINITY, -INFINITY, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 p = xy[i];
+        v.mn = fminf(v.mn, fminf(p.x, p.y));
+        v.mx = fmaxf(v.mx, fmaxf(p.x, p.y));
+    }
+    v.mn = warp_min(v.mn);
+    v.mx = warp_max(v.mx);
+    __shared__ float s_mn[32], s_mx[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { s_mn[w] = v.mn; s_mx[w] = v.mx; }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        float mn = lane < nw ? s_mn[lane] : INFINITY, mx = lane < nw ? s_mx[lane] : -INFINITY;
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0 && mn <= mx) {
+            atomicMin(&st->bbox[slot][0], f2ord(mn));
+            atomicMax(&st->bbox[slot][1], f2ord(mx));
+        }
+    }
+}
+
+// ---------------------------------------------------------------- attraction + update
+// alpha * sum_{j <-> i} (1 + beta / (1 + d^2)) (x_j - x_i), Eq. (newforce).
+__device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col, const float2* __restrict__ xy,
+                                             float alpha, float beta) {
+    float fx = 0.0f, fy = 0.0f;
+    const int e1 = rowptr[i + 1];
+    for (int e = rowptr[i]; e < e1; ++e) {
+        const float2 q = xy[__ldg(col + e)];
+        const float dx = q.x - p.x, dy = q.y - p.y;
+        const float c = 1.0f + beta / (1.0f + (dx * dx + dy * dy));
+        fx = fmaf(c, dx, fx);
+        fy = fmaf(c, dy, fy);
+    }
+    return make_float2(alpha * fx, alpha * fy);
+}
+
+// x + D min(1, s / |D|)
+__device__ __forceinline__ float2 capped_step(float2 p, float2 D, float s) {
+    const float nrm = sqrtf(D.x * D.x + D.y * D.y);
+    const float c = (nrm > s) ? s / nrm : 1.0f;
+    return make_float2(p.x + c * D.x, p.y + c * D.y);
+}
+
+// ---------------------------------------------------------------- FFT path: bin
+template <int K>
+__global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a, int advance) {
+    DevState* st = a.st;
+    const long long t = st->iter;
+    const int cur = (int)(t & 1);
+    const float2* __restrict__ xy = a.xy[cur];
+    const float lo = ord2f(st->bbox[cur][0]), hi = ord2f(st->bbox[cur][1]);
+    const DevParams prm = *a.prm;
+    const GridDesc g = make_grid(lo, hi, prm);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->grid = g;
+        st->t_cur = t;
+        st->step_cur = step_size(t, prm);
+        st->net_frep[0] = 0.0;
+        st->net_frep[1] = 0.0;
+        if (advance) {
+            st->bbox[cur ^ 1][0] = kOrdMinInit;
+            st->bbox[cur ^ 1][1] = kOrdMaxInit;
+        }
+        const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
+                           st->spec_k == prm.k && st->spec_P == prm.P;
+        st->spec_dirty = valid ? 0 : 1;
+        if (!valid) {
+            st->spec_h = g.h;
+            st->spec_gamma = prm.gamma;
+            st->spec_k = prm.k;
+            st->spec_P = prm.P;
+            st->spec_valid = 1;
+            st->spec_builds += 1;
+        }
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const float2 p = xy[i];
+        float tq;
+        const int bx = box_of(p.x, g.lo_f, g.h_f, g.n_int, &tq);
+        const int by = box_of(p.y, g.lo_f, g.h_f, g.n_int, &tq);
+        const int key = by * g.n_int + bx;
+        const int slot = atomicAdd(a.cnt + key, 1);
+        a.keyslot[i] = make_int2(key, slot);
+    }
+}
+
+// ---------------------------------------------------------------- FFT path: scan
+__global__ void __launch_bounds__(kScanThreads) k_scan_partial(NodeLaunch a) {
+    const int n_int = a.st->grid.n_int;
+    const int nbox = n_int * n_int;
+    const int i0 = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    int v[kScanItems];
+    const int4* src = reinterpret_cast<const int4*>(a.cnt + i0);
+    const int4 c0 = src[0], c1 = src[1];
+    v[0] = c0.x; v[1] = c0.y; v[2] = c0.z; v[3] = c0.w;
+    v[4] = c1.x; v[5] = c1.y; v[6] = c1.z; v[7] = c1.w;
+    int tsum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (i0 + q >= nbox) v[q] = 0;
+        tsum += v[q];
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __shared__ int s_w[32];
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int x = s_w[lane];
+        int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        s_w[lane] = xi - x;
+    }
+    __syncthreads();
+    int run = s_w[w] + incl - tsum;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        if (i0 + q < nbox) a.off[i0 + q] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == kScanThreads - 1) a.bsum[blockIdx.x] = run;
+}
+
+// Exclusive scan of the block sums (at most kScanThreads of them), one CTA.
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(NodeLaunch a, int nblocks, int advance) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = threadIdx.x < nblocks ? a.bsum[threadIdx.x] : 0;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __shared__ int s_w[32];
+    if (lane == 31) s_w[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        const int v = s_w[lane];
+        int vi = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, vi, o);
+            if (lane >= o) vi += y;
+        }
+        s_w[lane] = vi - v;
+    }
+    __syncthreads();
+    if (threadIdx.x < nblocks) a.bsum[threadIdx.x] = s_w[w] + incl - x;
+    if (threadIdx.x == 0 && advance) a.st->iter = a.st->t_cur + 1;
+}
+
+__global__ void __launch_bounds__(kNodeThreads) k_scan_add(NodeLaunch a) {
+    const int n_int = a.st->grid.n_int;
+    const int nbox = n_int * n_int;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nbox) {
+        a.off[i] += a.bsum[i / kScanChunk];
+        a.cnt[i] = 0;
+    }
+    if (i == 0) a.off[nbox] = a.n;
+}
+
+// ---------------------------------------------------------------- FFT path: scatter
+__global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
+    const int cur = (int)(a.st->t_cur & 1);
+    const float2* __restrict__ xy = a.xy[cur];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const int2 ks = a.keyslot[i];
+        const int pos = a.off[ks.x] + ks.y;
+        if ((unsigned)pos >= (unsigned)a.n) {
+            atomicOr(&a.st->flags, FLAG_SORT_RANGE);
+            continue;
+        }
+        a.sxy[pos] = xy[i];
+        a.perm[pos] = i;
+    }
+}
+
+// ---------------------------------------------------------------- FFT path: spread
+// One thread per box: sum over the box's nodes (contiguous after the sort) of the
+// Lagrange weights w (rho) and of w times the offset to each grid node (m^x, m^y).
+template <int K>
+__global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
+    const GridDesc g = a.st->grid;
+    const int nbox = g.n_int * g.n_int;
+    const AxisGeom ag = axis_geom(g, K);
+    const size_t plane = (size_t)a.Gs * a.Gs;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
+        const int by = b / g.n_int;
+        const int bx = b - by * g.n_int;
+        float rho[K][K], mx[K][K], my[K][K];
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) rho[ly][lx] = mx[ly][lx] = my[ly][lx] = 0.0f;
+        const int s0 = max(a.off[b], 0);
+        const int s1 = min(a.off[b + 1], a.n);
+        for (int s = s0; s < s1; ++s) {
+            const float2 p = a.sxy[s];
+            float ox, oy;
+            box_offset(p.x, ag, &ox);
+            box_offset(p.y, ag, &oy);
+            float wx[K], wy[K], dx[K], dy[K];
+            lagrange<K>(ox / ag.h_hi, wx);
+            lagrange<K>(oy / ag.h_hi, wy);
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                dx[l] = ox - ((float)l + 0.5f) * ag.hk;
+                dy[l] = oy - ((float)l + 0.5f) * ag.hk;
+            }
+#pragma unroll
+            for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+                for (int lx = 0; lx < K; ++lx) {
+                    const float w = wx[lx] * wy[ly];
+                    rho[ly][lx] += w;
+                    mx[ly][lx] = fmaf(w, dx[lx], mx[ly][lx]);
+                    my[ly][lx] = fmaf(w, dy[ly], my[ly][lx]);
+                }
+        }
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) {
+                const size_t q = (size_t)(by * K + ly) * a.Gs + (bx * K + lx);
+                a.gin[q] = rho[ly][lx];
+                a.gin[plane + q] = mx[ly][lx];
+                a.gin[2 * plane + q] = my[ly][lx];
+            }
+    }
+}
+
+// ---------------------------------------------------------------- FFT path: gather
+// frep(i) = sum_p w_ip [ (x_i - y_p) A_p + O_p ]  (well-conditioned Eq. Fr1/Fr2),
+// then attraction and the capped step (EVAL = false) or outputs (EVAL = true).
+template <int K, bool EVAL>
+__global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a) {
+    DevState* st = a.st;
+    const long long t = st->t_cur;
+    const int cur = (int)(t & 1);
+    const float2* __restrict__ xin = a.xy[cur];
+    float2* __restrict__ xout = a.xy[cur ^ 1];
+    const GridDesc g = st->grid;
+    const AxisGeom ag = axis_geom(g, K);
+    const float step = (float)st->step_cur;
+    const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
+    BlockAcc acc{INFINITY, -INFINITY, 0.0, 0.0};
+    unsigned bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        const float2 p = xin[i];
+        float ox, oy;
+        const int bx = box_offset(p.x, ag, &ox);
+        const int by = box_offset(p.y, ag, &oy);
+        float wx[K], wy[K], dx[K], dy[K];
+        lagrange<K>(ox / ag.h_hi, wx);
+        lagrange<K>(oy / ag.h_hi, wy);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            dx[l] = ox - ((float)l + 0.5f) * ag.hk;
+            dy[l] = oy - ((float)l + 0.5f) * ag.hk;
+        }
+        float frx = 0.0f, fry = 0.0f;
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly) {
+            const float4* row = a.gout + (size_t)(by * K + ly) * a.Gs + bx * K;
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) {
+                const float4 v = __ldg(row + lx);  // (A, O^x, O^y, 0)
+                const float w = wx[lx] * wy[ly];
+                frx = fmaf(w, fmaf(dx[lx], v.x, v.y), frx);
+                fry = fmaf(w, fmaf(dy[ly], v.x, v.z), fry);
+            }
+        }
+        const float2 fa = attraction(i, p, a.rowptr, a.col, xin, alpha, beta);
+        acc.fx += (double)frx;
+        acc.fy += (double)fry;
+        if (EVAL) {
+            a.frep_out[i] = make_float2(frx, fry);
+            a.fatt_out[i] = fa;
+        } else {
+            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
+            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+            xout[i] = q;
+            acc.mn = fminf(acc.mn, fminf(q.x, q.y));
+            acc.mx = fmaxf(acc.mx, fmaxf(q.x, q.y));
+        }
+    }
+    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+    block_publish(acc, st, cur ^ 1, !EVAL);
+}
+
+// ---------------------------------------------------------------- exact path
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// K = (1 + d^2)^-gamma given u = 1 + d^2
+template <int GI>
+__device__ __forceinline__ float kernel_of(float u, float gamma) {
+    if (GI == 0) return ex2_approx(-gamma * lg2_approx(u));
+    const float r = rcp_approx(u);
+    float k = r;
+    if (GI >= 2) k = r * r;
+    if (GI >= 4) k = k * k;
+    if (GI >= 8) k = k * k;
+    return k;
+}
+
+// Tiled all-pairs repulsion: each CTA owns kNodeThreads targets and one chunk of the
+// sources (blockIdx.y), staging source tiles in shared memory. Partial sums per chunk
+// go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic).
+template <int GI>
+__global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advance) {
+    DevState* st = a.st;
+    const long long t = st->iter;
+    const int cur = (int)(t & 1);
+    const float2* __restrict__ xy = a.xy[cur];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        st->t_cur = t;
+        st->step_cur = step_size(t, *a.prm);
+        st->net_frep[0] = 0.0;
+        st->net_frep[1] = 0.0;
+        if (advance) {
+            st->bbox[cur ^ 1][0] = kOrdMinInit;
+            st->bbox[cur ^ 1][1] = kOrdMaxInit;
+        }
+    }
+    const float gamma = (float)a.prm->gamma;
+    __shared__ float2 tile[kNodeThreads];
+    const int i = blockIdx.x * kNodeThreads + threadIdx.x;
+    const float2 pi = (i < a.n) ? xy[i] : make_float2(0.f, 0.f);
+    const int csize = (a.n + a.nchunks - 1) / a.nchunks;
+    const int j0 = blockIdx.y * csize;
+    const int j1 = min(a.n, j0 + csize);
+    float fx = 0.0f, fy = 0.0f;
+    for (int s0 = j0; s0 < j1; s0 += kNodeThreads) {
+        const int j = s0 + threadIdx.x;
+        tile[threadIdx.x] = (j < j1) ? xy[j] : pi;
+        __syncthreads();
+        const int cnt = min(kNodeThreads, j1 - s0);
+        if (cnt == kNodeThreads) {
+#pragma unroll 8
+            for (int jj = 0; jj < kNodeThreads; ++jj) {
+                const float2 q = tile[jj];
+                const float dx = pi.x - q.x, dy = pi.y - q.y;
+                const float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                fx = fmaf(K, dx, fx);
+                fy = fmaf(K, dy, fy);
+            }
+        } else {
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float2 q = tile[jj];
+                const float dx = pi.x - q.x, dy = pi.y - q.y;
+                const float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                fx = fmaf(K, dx, fx);
+                fy = fmaf(K, dy, fy);
+            }
+        }
+        __syncthreads();
+    }
+    if (i < a.n) a.part[(size_t)blockIdx.y * a.n + i] = make_float2(fx, fy);
+}
+
+template <bool EVAL>
+__global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int advance) {
+    DevState* st = a.st;
+    const long long t = st->t_cur;
+    const int cur = (int)(t & 1);
+    const float2* __restrict__ xin = a.xy[cur];
+    float2* __restrict__ xout = a.xy[cur ^ 1];
+    const float step = (float)st->step_cur;
+    const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
+    BlockAcc acc{INFINITY, -INFINITY, 0.0, 0.0};
+    unsigned bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        float frx = 0.0f, fry = 0.0f;
+        for (int c = 0; c < a.nchunks; ++c) {
+            const float2 v = a.part[(size_t)c * a.n + i];
+            frx += v.x;
+            fry += v.y;
+        }
+        const float2 p = xin[i];
+        const float2 fa = attraction(i, p, a.rowptr, a.col, xin, alpha, beta);
+        acc.fx += (double)frx;
+        acc.fy += (double)fry;
+        if (EVAL) {
+            a.frep_out[i] = make_float2(frx, fry);
+            a.fatt_out[i] = fa;
+        } else {
+            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
+            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+            xout[i] = q;
+            acc.mn = fminf(acc.mn, fminf(q.x, q.y));
+            acc.mx = fmaxf(acc.mx, fmaxf(q.x, q.y));
+        }
+    }
+    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+    block_publish(acc, st, cur ^ 1, !EVAL);
+    if (!EVAL && advance && blockIdx.x == 0 && threadIdx.x == 0) st->iter = t + 1;
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int blocks_for(long long work, int threads) {
+    long long b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (1LL << 30)) b = (1LL << 30);
+    return (int)b;
+}
+
+cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    int blocks = blocks_for(a.n, kNodeThreads);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_bbox<<<blocks, kNodeThreads, 0, s>>>(a.xy[slot], a.n, a.st, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_sort(const NodeLaunch& a, int advance, cudaStream_t s) {
+    const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
+    if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
+    const int nb = blocks_for(a.n, kNodeThreads);
+    switch (a.k) {
+        case 1: k_bin<1><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        case 2: k_bin<2><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        case 3: k_bin<3><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        default: return cudaErrorInvalidValue;
+    }
+    k_scan_partial<<<scan_blocks, kScanThreads, 0, s>>>(a);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(a, scan_blocks, advance);
+    k_scan_add<<<blocks_for(a.nbox_max, kNodeThreads), kNodeThreads, 0, s>>>(a);
+    k_scatter<<<nb, kNodeThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s) {
+    const int bb = blocks_for(a.nbox_max, kNodeThreads);
+    switch (a.k) {
+        case 1: k_spread<1><<<bb, kNodeThreads, 0, s>>>(a); break;
+        case 2: k_spread<2><<<bb, kNodeThreads, 0, s>>>(a); break;
+        case 3: k_spread<3><<<bb, kNodeThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <int K>
+static void back_k(const NodeLaunch& a, int eval, cudaStream_t s) {
+    const int nb = blocks_for(a.n, kNodeThreads);
+    if (eval) k_gather_update<K, true><<<nb, kNodeThreads, 0, s>>>(a);
+    else k_gather_update<K, false><<<nb, kNodeThreads, 0, s>>>(a);
+}
+
+cudaError_t launch_fft_back(const NodeLaunch& a, int eval, cudaStream_t s) {
+    switch (a.k) {
+        case 1: back_k<1>(a, eval, s); break;
+        case 2: back_k<2>(a, eval, s); break;
+        case 3: back_k<3>(a, eval, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s) {
+    dim3 grid(blocks_for(a.n, kNodeThreads), a.nchunks);
+    switch (a.gamma_int) {
+        case 2: k_exact<2><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
+        case 4: k_exact<4><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
+        case 8: k_exact<8><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
+        default: k_exact<0><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_update(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
+    const int nb = blocks_for(a.n, kNodeThreads);
+    if (eval) k_edge_update<true><<<nb, kNodeThreads, 0, s>>>(a, advance);
+    else k_edge_update<false><<<nb, kNodeThreads, 0, s>>>(a, advance);
+    return cudaGetLastError();
+}
+
+}  // namespace tfdp

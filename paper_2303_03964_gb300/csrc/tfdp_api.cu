@@ -1,0 +1,750 @@
+// tfdp_api.cu -- C ABI of the t-FDP library (declared in include/tfdp.h).
+//
+// A graph owns two device arenas: the node arena (positions, CSR, exact-path partial
+// sums, force outputs, parameters, state) and the FFT arena (sort buffers, grids,
+// transforms, spectrum, twiddles), sized by grid_max and k. Iterations are captured
+// once into CUDA graphs on a private stream and replayed on the caller's stream; the
+// kernels read the iteration counter, the grid and the step from device state, so
+// one captured graph serves every iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tfdp.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace tfdp;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+tfdp_status cuda_fail(cudaError_t e, const char* where) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    g_cuda_err = buf;
+    return e == cudaErrorMemoryAllocation ? TFDP_ERR_OUT_OF_MEMORY : TFDP_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);        \
+    } while (0)
+
+constexpr int kBatchIters = 8;  // iterations per captured multi-iteration graph
+constexpr int kMinLogP = 7, kMaxLogP = 13;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Sub-allocation plan inside one cudaMalloc.
+struct Arena {
+    size_t bytes = 0;
+    char* base = nullptr;
+    size_t take(size_t n) {
+        size_t off = align_up(bytes, 256);
+        bytes = off + align_up(n ? n : 1, 256);
+        return off;
+    }
+};
+
+int gamma_int_of(double g) {
+    double r = std::floor(g + 0.5);
+    if (std::fabs(g - r) == 0.0 && r >= 2.0 && r <= 8.0) return (int)r;
+    return 0;
+}
+
+int log2_ceil(long long v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct tfdp_graph {
+    int64_t n = 0, m = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;      // caller's stream
+    cudaStream_t cap_stream = nullptr;  // private, for graph capture
+    tfdp_params params{};
+    DevParams dp{};
+    int64_t host_iter = 0;
+
+    // node arena
+    void* node_mem = nullptr;
+    float2* xy[2] = {nullptr, nullptr};
+    int* rowptr = nullptr;
+    int* col = nullptr;
+    float2* part = nullptr;
+    int nchunks = 1;
+    float2* frep_buf = nullptr;
+    float2* fatt_buf = nullptr;
+    DevParams* dprm = nullptr;
+    DevState* dst = nullptr;
+
+    // FFT arena
+    void* fft_mem = nullptr;
+    int fft_k = 0, fft_grid_max = 0;  // what the FFT arena was sized for
+    int P = 0, logP = 0, G_max = 0, Gs = 0, ystride = 0, nbox_max = 0;
+    int* cnt = nullptr;
+    int* off = nullptr;
+    int* bsum = nullptr;
+    int2* keyslot = nullptr;
+    float2* sxy = nullptr;
+    int* perm = nullptr;
+    float* gin = nullptr;
+    float2* T1 = nullptr;
+    float2* T2 = nullptr;
+    float4* gout = nullptr;
+    float2* S1 = nullptr;
+    float* specK = nullptr;
+    float* specHx = nullptr;
+    float* specHy = nullptr;
+    float2* tw = nullptr;
+
+    // captured iterations
+    cudaGraphExec_t exec1 = nullptr, execB = nullptr;
+    long long exec_key = -1;
+
+    // stage timing (events around the stages of an iteration)
+    bool timing = false;
+    cudaEvent_t ev[TFDP_NUM_STAGES + 1] = {};
+
+    NodeLaunch node_launch() const {
+        NodeLaunch a{};
+        a.n = (int)n;
+        a.k = params.k_interp;
+        a.gamma_int = dp.gamma_int;
+        a.xy[0] = xy[0];
+        a.xy[1] = xy[1];
+        a.rowptr = rowptr;
+        a.col = col;
+        a.st = dst;
+        a.prm = dprm;
+        a.nbox_max = nbox_max;
+        a.cnt = cnt;
+        a.off = off;
+        a.bsum = bsum;
+        a.keyslot = keyslot;
+        a.sxy = sxy;
+        a.perm = perm;
+        a.gin = gin;
+        a.Gs = Gs;
+        a.gout = gout;
+        a.part = part;
+        a.nchunks = nchunks;
+        a.frep_out = frep_buf;
+        a.fatt_out = fatt_buf;
+        return a;
+    }
+    FftLaunch fft_launch() const {
+        FftLaunch f{};
+        f.logP = logP;
+        f.G_max = G_max;
+        f.Gs = Gs;
+        f.ystride = ystride;
+        f.gin = gin;
+        f.T1 = T1;
+        f.T2 = T2;
+        f.gout = gout;
+        f.S1 = S1;
+        f.specK = specK;
+        f.specHx = specHx;
+        f.specHy = specHy;
+        f.tw = tw;
+        f.st = dst;
+        f.prm = dprm;
+        return f;
+    }
+};
+
+namespace {
+
+DevParams make_dev_params(const tfdp_params& p, int P, int logP) {
+    DevParams d{};
+    d.alpha = p.alpha;
+    d.beta = p.beta;
+    d.gamma = p.gamma;
+    d.step0 = p.step0;
+    d.step_min = p.step_min;
+    d.k = p.k_interp;
+    d.n_int_min = p.n_int_min;
+    d.grid_max = p.grid_max;
+    d.policy = p.grid_policy;
+    d.total_iters = p.total_iters;
+    d.P = P;
+    d.log2P = logP;
+    d.gamma_int = gamma_int_of(p.gamma);
+    return d;
+}
+
+// FFT geometry implied by the parameters.
+bool fft_geometry(const tfdp_params& p, int* P, int* logP, int* G_max, int* nbox_max) {
+    const int n_int_max = p.grid_max / p.k_interp;
+    if (n_int_max < 1) return false;
+    const int G = n_int_max * p.k_interp;
+    int l = log2_ceil(2LL * G - 1);
+    if (l < kMinLogP) l = kMinLogP;
+    if (l > kMaxLogP) return false;
+    *logP = l;
+    *P = 1 << l;
+    *G_max = G;
+    *nbox_max = n_int_max * n_int_max;
+    return true;
+}
+
+void free_execs(tfdp_graph* g) {
+    if (g->exec1) cudaGraphExecDestroy(g->exec1);
+    if (g->execB) cudaGraphExecDestroy(g->execB);
+    g->exec1 = g->execB = nullptr;
+    g->exec_key = -1;
+}
+
+tfdp_status alloc_fft(tfdp_graph* g) {
+    int P, logP, G_max, nbox_max;
+    if (!fft_geometry(g->params, &P, &logP, &G_max, &nbox_max)) return TFDP_ERR_PARAM_RANGE;
+    const int chunk = scan_items_per_block();
+    const int scan_blocks = (nbox_max + chunk - 1) / chunk;
+    if (scan_blocks > 1024) return TFDP_ERR_PARAM_RANGE;
+    if (g->fft_mem && g->P == P && g->nbox_max == nbox_max && g->G_max == G_max) return TFDP_OK;
+    if (g->fft_mem) {
+        CK(cudaStreamSynchronize(g->stream));
+        CK(cudaFree(g->fft_mem));
+        g->fft_mem = nullptr;
+    }
+    free_execs(g);
+    const int Gs = (int)align_up((size_t)G_max, 4);
+    const size_t NH = (size_t)P / 2 + 1;
+    const size_t n = (size_t)std::max<int64_t>(g->n, 1);
+    Arena A;
+    size_t o_cnt = A.take(sizeof(int) * (size_t)scan_blocks * chunk);
+    size_t o_off = A.take(sizeof(int) * ((size_t)nbox_max + 1));
+    size_t o_bsum = A.take(sizeof(int) * 1024);
+    size_t o_ks = A.take(sizeof(int2) * n);
+    size_t o_sxy = A.take(sizeof(float2) * n);
+    size_t o_perm = A.take(sizeof(int) * n);
+    size_t o_gin = A.take(sizeof(float) * 3 * (size_t)Gs * Gs);
+    size_t o_T1 = A.take(sizeof(float2) * 3 * NH * Gs);
+    size_t o_T2 = A.take(sizeof(float2) * 3 * NH * Gs);
+    size_t o_gout = A.take(sizeof(float4) * (size_t)Gs * Gs);
+    size_t o_S1 = A.take(sizeof(float2) * 3 * NH * P);
+    size_t o_sK = A.take(sizeof(float) * NH * P);
+    size_t o_sHx = A.take(sizeof(float) * NH * P);
+    size_t o_sHy = A.take(sizeof(float) * NH * P);
+    size_t o_tw = A.take(sizeof(float2) * P);
+    void* mem = nullptr;
+    CK(prepare_fft(logP));
+    cudaError_t e = cudaMalloc(&mem, A.bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fft arena)");
+    char* b = (char*)mem;
+    g->fft_mem = mem;
+    g->cnt = (int*)(b + o_cnt);
+    g->off = (int*)(b + o_off);
+    g->bsum = (int*)(b + o_bsum);
+    g->keyslot = (int2*)(b + o_ks);
+    g->sxy = (float2*)(b + o_sxy);
+    g->perm = (int*)(b + o_perm);
+    g->gin = (float*)(b + o_gin);
+    g->T1 = (float2*)(b + o_T1);
+    g->T2 = (float2*)(b + o_T2);
+    g->gout = (float4*)(b + o_gout);
+    g->S1 = (float2*)(b + o_S1);
+    g->specK = (float*)(b + o_sK);
+    g->specHx = (float*)(b + o_sHx);
+    g->specHy = (float*)(b + o_sHy);
+    g->tw = (float2*)(b + o_tw);
+    g->P = P;
+    g->logP = logP;
+    g->G_max = G_max;
+    g->Gs = Gs;
+    g->ystride = Gs;
+    g->nbox_max = nbox_max;
+    g->fft_k = g->params.k_interp;
+    g->fft_grid_max = g->params.grid_max;
+    CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * (size_t)scan_blocks * chunk, g->stream));
+    CK(cudaMemsetAsync(g->gin, 0, sizeof(float) * 3 * (size_t)Gs * Gs, g->stream));
+    std::vector<float2> tw(P);
+    const double pi = 3.14159265358979323846;
+    for (int t = 0; t < P; ++t) {
+        const double a = -2.0 * pi * (double)t / (double)P;
+        tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    CK(cudaMemcpyAsync(g->tw, tw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, g->stream));
+    // a new arena has no valid spectrum
+    CK(cudaMemsetAsync(&g->dst->spec_valid, 0, sizeof(int), g->stream));
+    CK(cudaStreamSynchronize(g->stream));  // keeps `tw` alive until copied
+    return TFDP_OK;
+}
+
+tfdp_status upload_params(tfdp_graph* g) {
+    g->dp = make_dev_params(g->params, g->P ? g->P : 128, g->logP ? g->logP : 7);
+    CK(cudaMemcpyAsync(g->dprm, &g->dp, sizeof(DevParams), cudaMemcpyHostToDevice, g->stream));
+    // dp lives in the graph object, which outlives the copy; the copy is ordered
+    // before any later kernel on the stream.
+    return TFDP_OK;
+}
+
+// Recompute the bbox slot of the current positions.
+tfdp_status refresh_bbox(tfdp_graph* g) {
+    const int slot = (int)(g->host_iter & 1);
+    const unsigned init[2] = {kOrdMinInit, kOrdMaxInit};
+    CK(cudaMemcpyAsync(&g->dst->bbox[slot][0], init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));  // `init` is a stack buffer
+    CK(launch_bbox(g->node_launch(), slot, g->stream));
+    return TFDP_OK;
+}
+
+// Enqueue one iteration (advance = 1) or one force evaluation (advance = 0, eval = 1).
+// With stage timing on, an event is recorded before the first stage and after each
+// stage (inside a captured graph these become event-record nodes).
+tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
+    const NodeLaunch a = g->node_launch();
+    const bool tm = g->timing;
+    int mark_i = 0;
+    auto mark = [&]() -> cudaError_t { return tm ? cudaEventRecord(g->ev[mark_i++], s) : cudaSuccess; };
+    CK(mark());
+    if (g->params.rep_mode == TFDP_REP_EXACT) {
+        CK(launch_exact_pairs(a, advance, s));
+        CK(mark());
+        CK(launch_edge_update(a, advance, eval, s));
+        CK(mark());
+    } else {
+        const FftLaunch f = g->fft_launch();
+        CK(launch_fft_sort(a, advance, s));
+        CK(mark());
+        CK(launch_fft_spread(a, s));
+        CK(mark());
+        CK(launch_spectrum(f, s));
+        CK(mark());
+        CK(launch_rows_fwd(f, s));
+        CK(mark());
+        CK(launch_cols(f, s));
+        CK(mark());
+        CK(launch_rows_inv(f, s));
+        CK(mark());
+        CK(launch_fft_back(a, eval, s));
+        CK(mark());
+    }
+    return TFDP_OK;
+}
+
+// Kernels launched per iteration (count of the launches above).
+int kernels_per_iteration(const tfdp_graph* g) {
+    return g->params.rep_mode == TFDP_REP_EXACT ? 2 : (5 + 1 + 2 + 1 + 1 + 1 + 1);
+}
+
+long long exec_key_of(const tfdp_graph* g) {
+    return ((long long)g->params.rep_mode << 40) | ((long long)g->params.k_interp << 32) |
+           ((long long)g->dp.gamma_int << 24) | ((long long)g->logP << 16) |
+           ((long long)g->timing << 8) | (long long)(g->fft_mem != nullptr);
+}
+
+tfdp_status capture(tfdp_graph* g, int iters, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
+    tfdp_status st = TFDP_OK;
+    for (int i = 0; i < iters && st == TFDP_OK; ++i) st = enqueue_step(g, g->cap_stream, 1, 0);
+    cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
+    if (st != TFDP_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return TFDP_OK;
+}
+
+tfdp_status ensure_execs(tfdp_graph* g) {
+    const long long key = exec_key_of(g);
+    if (g->exec1 && g->execB && g->exec_key == key) return TFDP_OK;
+    free_execs(g);
+    tfdp_status st = capture(g, 1, &g->exec1);
+    if (st != TFDP_OK) return st;
+    st = capture(g, kBatchIters, &g->execB);
+    if (st != TFDP_OK) return st;
+    g->exec_key = key;
+    return TFDP_OK;
+}
+
+uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tfdp_status_str(tfdp_status s) {
+    switch (s) {
+        case TFDP_OK: return "TFDP_OK";
+        case TFDP_ERR_INVALID_ARG: return "TFDP_ERR_INVALID_ARG";
+        case TFDP_ERR_BAD_GRAPH: return "TFDP_ERR_BAD_GRAPH";
+        case TFDP_ERR_PARAM_RANGE: return "TFDP_ERR_PARAM_RANGE";
+        case TFDP_ERR_OUT_OF_MEMORY: return "TFDP_ERR_OUT_OF_MEMORY";
+        case TFDP_ERR_CUDA: return "TFDP_ERR_CUDA";
+        case TFDP_ERR_TIMEOUT: return "TFDP_ERR_TIMEOUT";
+        case TFDP_ERR_BUSY: return "TFDP_ERR_BUSY";
+        case TFDP_ERR_DEVICE_CHECK: return "TFDP_ERR_DEVICE_CHECK";
+    }
+    return "TFDP_ERR_UNKNOWN";
+}
+
+const char* tfdp_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+tfdp_status tfdp_params_default(tfdp_params* out) {
+    if (!out) return TFDP_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->alpha = 0.1;
+    out->beta = 8.0;
+    out->gamma = 2.0;
+    out->k_interp = 3;
+    out->n_int_min = 50;
+    out->grid_max = 1023;
+    out->grid_policy = TFDP_GRID_SNAP_H;
+    out->rep_mode = TFDP_REP_FFT;
+    out->precision = TFDP_PREC_FP32;
+    out->step0 = 1.0;
+    out->step_min = 0.01;
+    out->total_iters = 300;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
+    if (!p) return TFDP_ERR_INVALID_ARG;
+    if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return TFDP_ERR_PARAM_RANGE;
+    if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return TFDP_ERR_PARAM_RANGE;
+    if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return TFDP_ERR_PARAM_RANGE;
+    if (p->k_interp < 1 || p->k_interp > kMaxK) return TFDP_ERR_PARAM_RANGE;
+    if (p->n_int_min < 1) return TFDP_ERR_PARAM_RANGE;
+    if (p->grid_max < p->k_interp) return TFDP_ERR_PARAM_RANGE;
+    if (p->grid_policy != TFDP_GRID_PAPER && p->grid_policy != TFDP_GRID_SNAP_H) return TFDP_ERR_INVALID_ARG;
+    if (p->rep_mode != TFDP_REP_EXACT && p->rep_mode != TFDP_REP_FFT) return TFDP_ERR_INVALID_ARG;
+    if (p->precision != TFDP_PREC_FP32) return TFDP_ERR_PARAM_RANGE;  // BF16X3: not built
+    if (!(p->step_min > 0.0) || !(p->step0 >= p->step_min) || !std::isfinite(p->step0)) return TFDP_ERR_PARAM_RANGE;
+    if (p->total_iters < 1) return TFDP_ERR_PARAM_RANGE;
+    for (int i = 0; i < 7; ++i)
+        if (p->reserved[i] != 0) return TFDP_ERR_INVALID_ARG;
+    if (p->rep_mode == TFDP_REP_FFT) {
+        int P, l, G, nb;
+        if (!fft_geometry(*p, &P, &l, &G, &nb)) return TFDP_ERR_PARAM_RANGE;
+        if ((nb + scan_items_per_block() - 1) / scan_items_per_block() > 1024) return TFDP_ERR_PARAM_RANGE;
+    }
+    if (weight_ok) *weight_ok = (p->alpha * (1.0 + p->beta) < 1.0) ? 1 : 0;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const float* xy0, uint64_t seed,
+                              const tfdp_params* params, void* stream, tfdp_graph** out) {
+    if (!out || n < 0 || m < 0 || (m > 0 && !edges)) return TFDP_ERR_INVALID_ARG;
+    if (n > (int64_t)INT32_MAX / 2 || 2 * m > (int64_t)INT32_MAX) return TFDP_ERR_INVALID_ARG;
+    tfdp_params p;
+    if (params) p = *params;
+    else tfdp_params_default(&p);
+    tfdp_status st = tfdp_params_check(&p, nullptr);
+    if (st != TFDP_OK) return st;
+
+    // validate edges and build the symmetric CSR (rows sorted by neighbour id)
+    std::vector<int64_t> keys((size_t)m);
+    std::vector<int> deg((size_t)n + 1, 0);
+    for (int64_t q = 0; q < m; ++q) {
+        const int64_t a = edges[2 * q], b = edges[2 * q + 1];
+        if (a < 0 || b < 0 || a >= n || b >= n || a == b) return TFDP_ERR_BAD_GRAPH;
+        keys[(size_t)q] = std::min(a, b) * n + std::max(a, b);
+        deg[(size_t)a]++;
+        deg[(size_t)b]++;
+    }
+    std::sort(keys.begin(), keys.end());
+    for (size_t q = 1; q < keys.size(); ++q)
+        if (keys[q] == keys[q - 1]) return TFDP_ERR_BAD_GRAPH;
+    std::vector<int> rowptr((size_t)n + 1, 0);
+    for (int64_t i = 0; i < n; ++i) rowptr[(size_t)i + 1] = rowptr[(size_t)i] + deg[(size_t)i];
+    std::vector<int> col((size_t)(2 * m));
+    std::vector<int> fill(rowptr.begin(), rowptr.end() - 1);
+    for (int64_t q = 0; q < m; ++q) {
+        const int a = edges[2 * q], b = edges[2 * q + 1];
+        col[(size_t)fill[(size_t)a]++] = b;
+        col[(size_t)fill[(size_t)b]++] = a;
+    }
+    for (int64_t i = 0; i < n; ++i) std::sort(col.begin() + rowptr[(size_t)i], col.begin() + rowptr[(size_t)i + 1]);
+
+    tfdp_graph* g = new (std::nothrow) tfdp_graph();
+    if (!g) return TFDP_ERR_OUT_OF_MEMORY;
+    g->n = n;
+    g->m = m;
+    g->params = p;
+    g->stream = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "create stream");
+    }
+
+    // exact-path chunking: about four CTAs per SM in total
+    const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
+    g->nchunks = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    Arena A;
+    size_t o_xy0 = A.take(sizeof(float2) * nn);
+    size_t o_xy1 = A.take(sizeof(float2) * nn);
+    size_t o_rp = A.take(sizeof(int) * (nn + 1));
+    size_t o_col = A.take(sizeof(int) * (size_t)std::max<int64_t>(2 * m, 1));
+    size_t o_part = A.take(sizeof(float2) * nn * (size_t)g->nchunks);
+    size_t o_fr = A.take(sizeof(float2) * nn);
+    size_t o_fa = A.take(sizeof(float2) * nn);
+    size_t o_prm = A.take(sizeof(DevParams));
+    size_t o_st = A.take(sizeof(DevState));
+    e = cudaMalloc(&g->node_mem, A.bytes);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(g->cap_stream);
+        delete g;
+        return cuda_fail(e, "cudaMalloc(node arena)");
+    }
+    char* b = (char*)g->node_mem;
+    g->xy[0] = (float2*)(b + o_xy0);
+    g->xy[1] = (float2*)(b + o_xy1);
+    g->rowptr = (int*)(b + o_rp);
+    g->col = (int*)(b + o_col);
+    g->part = (float2*)(b + o_part);
+    g->frep_buf = (float2*)(b + o_fr);
+    g->fatt_buf = (float2*)(b + o_fa);
+    g->dprm = (DevParams*)(b + o_prm);
+    g->dst = (DevState*)(b + o_st);
+
+    auto fail = [&](tfdp_status s) {
+        tfdp_destroy_graph(g);
+        return s;
+    };
+    std::vector<float> init;
+    const float* src = xy0;
+    if (!src && n > 0) {
+        init.resize((size_t)(2 * n));
+        const double half = 0.5 * std::sqrt((double)n);
+        for (int64_t i = 0; i < 2 * n; ++i) {
+            const uint64_t z = splitmix64(seed + (uint64_t)i * 0x9E3779B97F4A7C15ULL);
+            const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+            init[(size_t)i] = (float)((2.0 * u - 1.0) * half);
+        }
+        src = init.data();
+    }
+    if ((e = cudaMemsetAsync(g->dst, 0, sizeof(DevState), g->stream)) != cudaSuccess) return fail(cuda_fail(e, "memset state"));
+    if (n > 0) {
+        if ((e = cudaMemcpyAsync(g->xy[0], src, sizeof(float2) * (size_t)n, cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+            return fail(cuda_fail(e, "copy positions"));
+        if ((e = cudaMemcpyAsync(g->rowptr, rowptr.data(), sizeof(int) * (size_t)(n + 1), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+            return fail(cuda_fail(e, "copy rowptr"));
+    }
+    if (m > 0 && (e = cudaMemcpyAsync(g->col, col.data(), sizeof(int) * (size_t)(2 * m), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+        return fail(cuda_fail(e, "copy col"));
+    if (p.rep_mode == TFDP_REP_FFT) {
+        st = alloc_fft(g);
+        if (st != TFDP_OK) return fail(st);
+    }
+    st = upload_params(g);
+    if (st == TFDP_OK) st = refresh_bbox(g);  // synchronises: host buffers above are consumed
+    if (st != TFDP_OK) return fail(st);
+    *out = g;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
+    if (!g || !p) return TFDP_ERR_INVALID_ARG;
+    tfdp_status st = tfdp_params_check(p, nullptr);
+    if (st != TFDP_OK) return st;
+    g->params = *p;
+    if (p->rep_mode == TFDP_REP_FFT) {
+        st = alloc_fft(g);
+        if (st != TFDP_OK) return st;
+    }
+    st = upload_params(g);
+    if (st != TFDP_OK) return st;
+    CK(cudaStreamSynchronize(g->stream));  // g->dp may change again before the copy runs
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_get_params(const tfdp_graph* g, tfdp_params* out) {
+    if (!g || !out) return TFDP_ERR_INVALID_ARG;
+    *out = g->params;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_set_positions(tfdp_graph* g, const float* xy, int on_device) {
+    if (!g || (!xy && g->n > 0)) return TFDP_ERR_INVALID_ARG;
+    if (g->n == 0) return TFDP_OK;
+    const int slot = (int)(g->host_iter & 1);
+    CK(cudaMemcpyAsync(g->xy[slot], xy, sizeof(float2) * (size_t)g->n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    return refresh_bbox(g);
+}
+
+tfdp_status tfdp_get_positions(tfdp_graph* g, float* xy, int on_device) {
+    if (!g || (!xy && g->n > 0)) return TFDP_ERR_INVALID_ARG;
+    if (g->n > 0) {
+        const int slot = (int)(g->host_iter & 1);
+        CK(cudaMemcpyAsync(xy, g->xy[slot], sizeof(float2) * (size_t)g->n,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
+    if (!g || iters < 0) return TFDP_ERR_INVALID_ARG;
+    if (iters == 0) return TFDP_OK;
+    if (g->n == 0) {
+        g->host_iter += iters;
+        return tfdp_set_iteration(g, g->host_iter);
+    }
+    tfdp_status st = ensure_execs(g);
+    if (st != TFDP_OK) return st;
+    int left = iters;
+    while (left >= kBatchIters) {
+        CK(cudaGraphLaunch(g->execB, g->stream));
+        left -= kBatchIters;
+    }
+    while (left-- > 0) CK(cudaGraphLaunch(g->exec1, g->stream));
+    g->host_iter += iters;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_set_iteration(tfdp_graph* g, int64_t t) {
+    if (!g || t < 0) return TFDP_ERR_INVALID_ARG;
+    const int old_slot = (int)(g->host_iter & 1), new_slot = (int)(t & 1);
+    if (old_slot != new_slot && g->n > 0)
+        CK(cudaMemcpyAsync(g->xy[new_slot], g->xy[old_slot], sizeof(float2) * (size_t)g->n,
+                           cudaMemcpyDeviceToDevice, g->stream));
+    g->host_iter = t;
+    long long tt = (long long)t;
+    CK(cudaMemcpyAsync(&g->dst->iter, &tt, sizeof(tt), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (g->n > 0 && old_slot != new_slot) return refresh_bbox(g);
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_device) {
+    if (!g) return TFDP_ERR_INVALID_ARG;
+    if (g->n == 0) return TFDP_OK;
+    tfdp_status st = enqueue_step(g, g->stream, 0, 1);
+    if (st != TFDP_OK) return st;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (frep) CK(cudaMemcpyAsync(frep, g->frep_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
+    if (fatt) CK(cudaMemcpyAsync(fatt, g->fatt_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
+    if (!g || !out) return TFDP_ERR_INVALID_ARG;
+    DevState s;
+    CK(cudaMemcpyAsync(&s, g->dst, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->iteration = s.iter;
+    out->net_frep[0] = s.net_frep[0];
+    out->net_frep[1] = s.net_frep[1];
+    out->grid_lo = s.grid.lo;
+    out->grid_h = s.grid.h;
+    out->grid_n_int = s.grid.n_int;
+    out->grid_G = s.grid.G;
+    out->fft_P = g->P;
+    out->spectrum_builds = s.spec_builds;
+    out->device_flags = (int32_t)s.flags;
+    out->kernels_per_iteration = kernels_per_iteration(g);
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable) {
+    if (!g) return TFDP_ERR_INVALID_ARG;
+    if (enable && !g->ev[0]) {
+        for (int i = 0; i <= TFDP_NUM_STAGES; ++i) CK(cudaEventCreate(&g->ev[i]));
+    }
+    if ((bool)enable != g->timing) {
+        g->timing = enable != 0;
+        free_execs(g);  // recapture with / without the event nodes
+    }
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages) {
+    if (!g || !ms || nstages < 1) return TFDP_ERR_INVALID_ARG;
+    if (!g->timing) return TFDP_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(g->stream));
+    for (int i = 0; i < nstages; ++i) ms[i] = 0.0f;
+    const int used = g->params.rep_mode == TFDP_REP_EXACT ? 2 : 7;
+    const int base = g->params.rep_mode == TFDP_REP_EXACT ? TFDP_STAGE_EXACT : 0;
+    for (int i = 0; i < used; ++i) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, g->ev[i], g->ev[i + 1]));
+        if (base + i < nstages) ms[base + i] = t;
+    }
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_synchronize(tfdp_graph* g) {
+    if (!g) return TFDP_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(g->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
+    if (!g) return TFDP_OK;
+    if (g->stream || g->cap_stream) cudaStreamSynchronize(g->stream);
+    free_execs(g);
+    for (int i = 0; i <= TFDP_NUM_STAGES; ++i)
+        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    if (g->fft_mem) cudaFree(g->fft_mem);
+    if (g->node_mem) cudaFree(g->node_mem);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    delete g;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_debug_fetch(tfdp_graph* g, int what, void* dst, size_t bytes) {
+    if (!g || !dst) return TFDP_ERR_INVALID_ARG;
+    DevState s;
+    CK(cudaMemcpyAsync(&s, g->dst, sizeof(DevState), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const size_t G = (size_t)s.grid.G;
+    if (what == TFDP_DEBUG_SORT_PERM) {
+        if (!g->perm || bytes < sizeof(int) * (size_t)g->n) return TFDP_ERR_INVALID_ARG;
+        CK(cudaMemcpy(dst, g->perm, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToHost));
+        return TFDP_OK;
+    }
+    if (what == TFDP_DEBUG_CELL_START) {
+        const size_t nb = (size_t)s.grid.n_int * s.grid.n_int + 1;
+        if (!g->off || bytes < sizeof(int) * nb) return TFDP_ERR_INVALID_ARG;
+        CK(cudaMemcpy(dst, g->off, sizeof(int) * nb, cudaMemcpyDeviceToHost));
+        return TFDP_OK;
+    }
+    if (what == TFDP_DEBUG_GRID_CHARGES) {
+        if (!g->gin || bytes < sizeof(float) * 3 * G * G) return TFDP_ERR_INVALID_ARG;
+        for (int c = 0; c < 3; ++c)
+            CK(cudaMemcpy2D((char*)dst + sizeof(float) * G * G * c, sizeof(float) * G,
+                            g->gin + (size_t)c * g->Gs * g->Gs, sizeof(float) * g->Gs, sizeof(float) * G, G,
+                            cudaMemcpyDeviceToHost));
+        return TFDP_OK;
+    }
+    if (what == TFDP_DEBUG_GRID_OUTPUT) {
+        if (!g->gout || bytes < sizeof(float4) * G * G) return TFDP_ERR_INVALID_ARG;
+        CK(cudaMemcpy2D(dst, sizeof(float4) * G, g->gout, sizeof(float4) * g->Gs, sizeof(float4) * G, G,
+                        cudaMemcpyDeviceToHost));
+        return TFDP_OK;
+    }
+    return TFDP_ERR_INVALID_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+"""Python binding of the t-FDP C ABI (include/tfdp.h): argument marshalling only.
+
+Every step of an iteration runs in the CUDA library libtfdp.so; this module converts
+numpy arrays / torch tensors to pointers and status codes to exceptions. Importing it
+raises if the library has not been built (``__graft_entry__.build()`` or
+``python paper_2303_03964_gb300/build.py``): there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtfdp.so")
+
+REP_EXACT, REP_FFT = 0, 1
+PREC_FP32, PREC_BF16X3 = 0, 1
+GRID_PAPER, GRID_SNAP_H = 0, 1
+DEBUG_GRID_CHARGES, DEBUG_GRID_OUTPUT, DEBUG_SORT_PERM, DEBUG_CELL_START = 1, 2, 3, 4
+STAGES = ["sort", "spread", "spectrum", "rows_fwd", "cols", "rows_inv", "gather_update",
+          "exact", "edge_update"]
+
+STATUS = {0: "TFDP_OK", 1: "TFDP_ERR_INVALID_ARG", 2: "TFDP_ERR_BAD_GRAPH",
+          3: "TFDP_ERR_PARAM_RANGE", 4: "TFDP_ERR_OUT_OF_MEMORY", 5: "TFDP_ERR_CUDA",
+          6: "TFDP_ERR_TIMEOUT", 7: "TFDP_ERR_BUSY", 8: "TFDP_ERR_DEVICE_CHECK"}
+
+
+class TfdpError(RuntimeError):
+    def __init__(self, status, where, detail=""):
+        self.status = status
+        self.name = STATUS.get(status, "TFDP_ERR_%d" % status)
+        super().__init__("%s failed: %s%s" % (where, self.name, (" (" + detail + ")") if detail else ""))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("k_interp", ctypes.c_int32), ("n_int_min", ctypes.c_int32),
+                ("grid_max", ctypes.c_int32), ("grid_policy", ctypes.c_int32),
+                ("rep_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("step0", ctypes.c_double), ("step_min", ctypes.c_double),
+                ("total_iters", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int64), ("net_frep", ctypes.c_double * 2),
+                ("grid_lo", ctypes.c_double), ("grid_h", ctypes.c_double),
+                ("grid_n_int", ctypes.c_int32), ("grid_G", ctypes.c_int32),
+                ("fft_P", ctypes.c_int32), ("spectrum_builds", ctypes.c_int32),
+                ("device_flags", ctypes.c_int32), ("kernels_per_iteration", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["net_frep"] = (self.net_frep[0], self.net_frep[1])
+        return d
+
+
+_p = ctypes.c_void_p
+_SIGS = {
+    "tfdp_status_str": ([ctypes.c_int], ctypes.c_char_p),
+    "tfdp_last_cuda_error": ([], ctypes.c_char_p),
+    "tfdp_params_default": ([ctypes.POINTER(Params)], ctypes.c_int),
+    "tfdp_params_check": ([ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "tfdp_create_graph": ([ctypes.c_int64, ctypes.c_int64, _p, _p, ctypes.c_uint64,
+                           ctypes.POINTER(Params), _p, ctypes.POINTER(_p)], ctypes.c_int),
+    "tfdp_set_params": ([_p, ctypes.POINTER(Params)], ctypes.c_int),
+    "tfdp_get_params": ([_p, ctypes.POINTER(Params)], ctypes.c_int),
+    "tfdp_set_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_get_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_iterate": ([_p, ctypes.c_int32], ctypes.c_int),
+    "tfdp_set_iteration": ([_p, ctypes.c_int64], ctypes.c_int),
+    "tfdp_eval_forces": ([_p, _p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_get_stats": ([_p, ctypes.POINTER(Stats)], ctypes.c_int),
+    "tfdp_synchronize": ([_p], ctypes.c_int),
+    "tfdp_set_stage_timing": ([_p, ctypes.c_int], ctypes.c_int),
+    "tfdp_get_stage_times": ([_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
+    "tfdp_destroy_graph": ([_p], ctypes.c_int),
+    "tfdp_debug_fetch": ([_p, ctypes.c_int, _p, ctypes.c_size_t], ctypes.c_int),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtfdp.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _check(status, where):
+    if status != 0:
+        detail = lib.tfdp_last_cuda_error().decode() if status in (4, 5) else ""
+        raise TfdpError(status, where, detail)
+
+
+def params_default(**overrides) -> Params:
+    p = Params()
+    _check(lib.tfdp_params_default(ctypes.byref(p)), "tfdp_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def params_check(p: Params):
+    ok = ctypes.c_int(0)
+    _check(lib.tfdp_params_check(ctypes.byref(p), ctypes.byref(ok)), "tfdp_params_check")
+    return bool(ok.value)
+
+
+def _is_torch_cuda(x):
+    return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and x.is_cuda
+
+
+def _host_f32(x, n):
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(n, 2))
+    return a
+
+
+class Graph:
+    """One graph on the current CUDA device (wraps a tfdp_graph handle)."""
+
+    def __init__(self, n, edges, xy0=None, params=None, seed=0, stream=0):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        self.n = int(n)
+        self.m = int(e.shape[0])
+        self._edges = e
+        xp = None
+        if xy0 is not None:
+            xp = _host_f32(xy0, self.n)
+        self._params = params if params is not None else params_default()
+        h = _p()
+        st = lib.tfdp_create_graph(self.n, self.m, e.ctypes.data_as(_p) if self.m else None,
+                                   xp.ctypes.data_as(_p) if xp is not None else None,
+                                   ctypes.c_uint64(seed), ctypes.byref(self._params),
+                                   _p(stream or 0), ctypes.byref(h))
+        _check(st, "tfdp_create_graph")
+        self._h = h
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.tfdp_destroy_graph(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ parameters
+    def set_params(self, params: Params = None, **overrides):
+        p = Params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(params or self._params), ctypes.sizeof(Params))
+        for k, v in overrides.items():
+            setattr(p, k, v)
+        _check(lib.tfdp_set_params(self._h, ctypes.byref(p)), "tfdp_set_params")
+        self._params = p
+
+    def get_params(self) -> Params:
+        p = Params()
+        _check(lib.tfdp_get_params(self._h, ctypes.byref(p)), "tfdp_get_params")
+        return p
+
+    # ------------------------------------------------------------ positions
+    def set_positions(self, xy):
+        if _is_torch_cuda(xy):
+            assert xy.is_contiguous() and xy.numel() == 2 * self.n
+            _check(lib.tfdp_set_positions(self._h, _p(xy.data_ptr()), 1), "tfdp_set_positions")
+        else:
+            a = _host_f32(xy, self.n)
+            _check(lib.tfdp_set_positions(self._h, a.ctypes.data_as(_p), 0), "tfdp_set_positions")
+
+    def get_positions(self, out=None):
+        """Positions as an (n, 2) float32 numpy array, or into `out` (numpy or CUDA tensor)."""
+        if out is not None and _is_torch_cuda(out):
+            _check(lib.tfdp_get_positions(self._h, _p(out.data_ptr()), 1), "tfdp_get_positions")
+            return out
+        a = out if out is not None else np.empty((self.n, 2), dtype=np.float32)
+        _check(lib.tfdp_get_positions(self._h, a.ctypes.data_as(_p), 0), "tfdp_get_positions")
+        return a
+
+    # ------------------------------------------------------------ compute
+    def iterate(self, iters=1):
+        _check(lib.tfdp_iterate(self._h, int(iters)), "tfdp_iterate")
+
+    def set_iteration(self, t):
+        _check(lib.tfdp_set_iteration(self._h, int(t)), "tfdp_set_iteration")
+
+    def eval_forces(self):
+        """(frep, fatt) at the current positions, each (n, 2) float32."""
+        fr = np.empty((self.n, 2), dtype=np.float32)
+        fa = np.empty((self.n, 2), dtype=np.float32)
+        _check(lib.tfdp_eval_forces(self._h, fr.ctypes.data_as(_p), fa.ctypes.data_as(_p), 0),
+               "tfdp_eval_forces")
+        return fr, fa
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib.tfdp_get_stats(self._h, ctypes.byref(s)), "tfdp_get_stats")
+        return s.as_dict()
+
+    def set_stage_timing(self, enable=True):
+        _check(lib.tfdp_set_stage_timing(self._h, 1 if enable else 0), "tfdp_set_stage_timing")
+
+    def stage_times(self) -> dict:
+        ms = (ctypes.c_float * len(STAGES))()
+        _check(lib.tfdp_get_stage_times(self._h, ms, len(STAGES)), "tfdp_get_stage_times")
+        return {name: float(ms[i]) for i, name in enumerate(STAGES)}
+
+    def synchronize(self):
+        _check(lib.tfdp_synchronize(self._h), "tfdp_synchronize")
+
+    def debug_fetch(self, what):
+        s = self.stats()
+        G, n_int = s["grid_G"], s["grid_n_int"]
+        if what == DEBUG_GRID_CHARGES:
+            a = np.empty((3, G, G), dtype=np.float32)
+        elif what == DEBUG_GRID_OUTPUT:
+            a = np.empty((G, G, 4), dtype=np.float32)
+        elif what == DEBUG_SORT_PERM:
+            a = np.empty(self.n, dtype=np.int32)
+        elif what == DEBUG_CELL_START:
+            a = np.empty(n_int * n_int + 1, dtype=np.int32)
+        else:
+            raise ValueError(what)
+        _check(lib.tfdp_debug_fetch(self._h, int(what), a.ctypes.data_as(_p), a.nbytes),
+               "tfdp_debug_fetch")
+        return a

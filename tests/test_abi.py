@@ -1,0 +1,75 @@
+"""CPU-only checks of the C ABI: the library loads, exports every symbol that
+include/tfdp.h declares, and its host-side validation behaves as documented.
+No call here launches a kernel."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2303_03964_gb300 import tfdp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tfdp_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    names = _declared_functions()
+    assert len(names) >= 15
+    out = os.popen("nm -D --defined-only %s" % tfdp.LIB_PATH).read()
+    exported = set(re.findall(r" T (tfdp_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(tfdp.lib, n)
+
+
+def test_params_default_values_are_the_papers():
+    p = tfdp.params_default()
+    assert (p.alpha, p.beta, p.gamma) == (0.1, 8.0, 2.0)
+    assert p.k_interp == 3 and p.n_int_min == 50
+    assert tfdp.params_check(p) is True  # alpha (1 + beta) = 0.9 < 1
+
+
+@pytest.mark.parametrize("field,value,status", [
+    ("gamma", 1.0, 3), ("gamma", 0.5, 3), ("alpha", -0.1, 3), ("beta", -1.0, 3),
+    ("k_interp", 0, 3), ("k_interp", 4, 3), ("grid_max", 2, 3), ("total_iters", 0, 3),
+    ("step_min", 0.0, 3), ("grid_policy", 7, 1), ("rep_mode", 5, 1), ("grid_max", 1 << 20, 3),
+])
+def test_params_range_rejected(field, value, status):
+    p = tfdp.params_default(**{field: value})
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.params_check(p)
+    assert ei.value.status == status
+
+
+def test_soft_weight_condition_is_flagged_not_rejected():
+    # Sec. 3.3 shows alpha = 0.5 with beta = 8, which breaks alpha (1 + beta) < 1
+    assert tfdp.params_check(tfdp.params_default(alpha=0.5)) is False
+
+
+@pytest.mark.parametrize("edges", [
+    [[0, 1], [1, 1]],          # self-loop
+    [[0, 1], [1, 0]],          # duplicate in the other order
+    [[0, 1], [0, 1]],          # duplicate
+    [[0, 3]],                  # out of range
+    [[-1, 2]],                 # negative id
+])
+def test_bad_graph_rejected_before_any_device_work(edges):
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.Graph(3, edges, np.zeros((3, 2), np.float32))
+    assert ei.value.status == 2
+
+
+def test_status_strings():
+    for code, name in tfdp.STATUS.items():
+        assert tfdp.lib.tfdp_status_str(code).decode() == name

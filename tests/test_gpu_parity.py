@@ -1,0 +1,283 @@
+"""GPU parity: the CUDA library (called through the C ABI) against the FP64 CPU oracle
+on identical seeded inputs.
+
+Tolerances:
+  * force fields: relative L2 <= 1e-5 against the oracle's own path (exact sum for the
+    exact kernel, the paper's ibFFT for the FFT path);
+  * short layouts with a fixed seed: relative L2 of positions <= 1e-4;
+  * integer work (box decision, sort, grid descriptor): bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_03964_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+POS_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def tfdp():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    from paper_2303_03964_gb300 import tfdp as t
+    return t
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _params(tfdp, **kw):
+    return tfdp.params_default(**kw)
+
+
+def _oracle_fft(xy32, stats, gamma, k, grid_max, policy, n_int_min=50):
+    g = oracle.grid_policy(xy32, k, n_int_min, grid_max, policy)
+    return g, oracle.rep_fft(xy32.astype(np.float64), gamma, k, grid=g, P=stats["fft_P"],
+                             xy_f32=xy32)
+
+
+# ------------------------------------------------------------------ exact path
+
+def test_exact_forces_er2000(tfdp):
+    e, xy64 = synth.er_2000()
+    xy = xy64.astype(np.float32)
+    with tfdp.Graph(2000, e, xy, _params(tfdp, rep_mode=tfdp.REP_EXACT)) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    ref_r = oracle.rep_exact(xy.astype(np.float64), 2.0)
+    ref_a = oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)
+    assert rel_l2(fr, ref_r) <= FORCE_TOL
+    assert rel_l2(fa, ref_a) <= FORCE_TOL
+    assert abs(st["net_frep"][0]) + abs(st["net_frep"][1]) < 1e-4 * np.abs(ref_r).sum()
+
+
+@pytest.mark.parametrize("gamma", [2.0, 3.0, 4.0, 2.5, 8.0])
+def test_exact_forces_gamma_variants(tfdp, gamma):
+    rng = np.random.default_rng(5)
+    n = 777  # ragged against the 256-node tiles
+    e = synth.erdos_renyi(n, 2000, rng)
+    xy = rng.uniform(-8, 8, size=(n, 2)).astype(np.float32)
+    with tfdp.Graph(n, e, xy, _params(tfdp, rep_mode=tfdp.REP_EXACT, gamma=gamma, beta=3.0)) as g:
+        fr, fa = g.eval_forces()
+    assert rel_l2(fr, oracle.rep_exact(xy.astype(np.float64), gamma)) <= FORCE_TOL
+    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 3.0)) <= FORCE_TOL
+
+
+def test_exact_layout_er2000_100_iterations(tfdp):
+    """Config 1: ER n=2000, m=8000, exact repulsion, 100 iterations."""
+    e, xy64 = synth.er_2000()
+    xy = xy64.astype(np.float32)
+    T = 100
+    with tfdp.Graph(2000, e, xy, _params(tfdp, rep_mode=tfdp.REP_EXACT, total_iters=T)) as g:
+        g.iterate(T)
+        out = g.get_positions()
+        assert g.stats()["iteration"] == T
+    ref = oracle.iterate(xy.astype(np.float64), e, T, mode="exact", T=T)
+    assert rel_l2(out, ref) <= POS_TOL
+
+
+# ------------------------------------------------------------------ FFT path
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("policy", [0, 1])
+def test_fft_forces_small(tfdp, k, policy):
+    rng = np.random.default_rng(10 + k + 3 * policy)
+    n = 3001
+    e = synth.erdos_renyi(n, 6000, rng)
+    xy = rng.uniform(-30, 30, size=(n, 2)).astype(np.float32)
+    p = _params(tfdp, k_interp=k, grid_policy=policy, grid_max=255)
+    with tfdp.Graph(n, e, xy, p) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    grid, ref = _oracle_fft(xy, st, 2.0, k, 255, policy)
+    # the grid descriptor is decided identically on both sides
+    assert st["grid_n_int"] == grid["n_int"] and st["grid_h"] == grid["h"]
+    assert st["grid_lo"] == grid["lo"]
+    assert rel_l2(fr, ref) <= FORCE_TOL, rel_l2(fr, ref)
+    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
+
+
+def test_fft_forces_sbm_100k(tfdp):
+    """Config 2: SBM n=100k, 20 blocks, mean degree 10, k=3, grid up to 256^2."""
+    e, xy = synth.sbm_100k()
+    with tfdp.Graph(xy.shape[0], e, xy, _params(tfdp, grid_max=255)) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    assert st["fft_P"] == 512 and st["grid_G"] <= 255
+    _, ref = _oracle_fft(xy, st, 2.0, 3, 255, 1)
+    assert rel_l2(fr, ref) <= FORCE_TOL, rel_l2(fr, ref)
+    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
+
+
+def test_fft_forces_lattice_1m_full_size(tfdp):
+    """Config 3 (i): 1000 x 1000 lattice at the size and launch configuration the
+    benchmark times (k=3, grid up to 1023, P=2048). Full element-wise comparison with
+    the oracle's ibFFT; row-sampled interpolation error against the exact sum."""
+    e, xy = synth.lattice_1m()
+    n = xy.shape[0]
+    with tfdp.Graph(n, e, xy, _params(tfdp, grid_max=1023)) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    assert st["fft_P"] == 2048
+    _, ref = _oracle_fft(xy, st, 2.0, 3, 1023, 1)
+    assert rel_l2(fr, ref) <= FORCE_TOL, rel_l2(fr, ref)
+    rows = np.random.default_rng(0).choice(n, 500, replace=False)
+    ex = oracle.rep_exact(xy.astype(np.float64), 2.0, rows=rows)
+    interp_err = rel_l2(fr[rows], ex)
+    ref_err = rel_l2(ref[rows], ex)
+    # the GPU's distance to the exact sum is the oracle's (the stated interpolation
+    # error of this grid), up to the FP32 parity tolerance
+    assert abs(interp_err - ref_err) <= 1e-3 * ref_err + FORCE_TOL
+
+
+def test_fft_ba_2m_full_size(tfdp):
+    """Config 3 (ii): Barabasi-Albert n=2M, m0=3 (heavy-tailed degrees)."""
+    e, xy = synth.ba_2m()
+    n = xy.shape[0]
+    with tfdp.Graph(n, e, xy, _params(tfdp, grid_max=1023)) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    _, ref = _oracle_fft(xy, st, 2.0, 3, 1023, 1)
+    assert rel_l2(fr, ref) <= FORCE_TOL, rel_l2(fr, ref)
+    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
+
+
+def test_fft_sort_and_spread_units(tfdp):
+    rng = np.random.default_rng(3)
+    n = 2500
+    xy = rng.uniform(-20, 25, size=(n, 2)).astype(np.float32)
+    with tfdp.Graph(n, np.zeros((0, 2), np.int32), xy, _params(tfdp, grid_max=255)) as g:
+        g.eval_forces()
+        st = g.stats()
+        perm = g.debug_fetch(tfdp.DEBUG_SORT_PERM)
+        start = g.debug_fetch(tfdp.DEBUG_CELL_START)
+        charges = g.debug_fetch(tfdp.DEBUG_GRID_CHARGES)
+    n_int, lo, h = st["grid_n_int"], st["grid_lo"], st["grid_h"]
+    # perm is a permutation, boxes are contiguous and match the FP32 decision
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    bx = np.array([oracle.box_f32(x, lo, h, n_int) for x in xy[:, 0]])
+    by = np.array([oracle.box_f32(y, lo, h, n_int) for y in xy[:, 1]])
+    key = by * n_int + bx
+    assert np.all(np.diff(key[perm]) >= 0)
+    counts = np.bincount(key, minlength=n_int * n_int)
+    assert np.array_equal(np.diff(start), counts) and start[-1] == n
+    # spread: rho = sum of weights; sum over the grid of rho equals n (partition of unity)
+    assert abs(charges[0].sum() - n) < 1e-3 * n
+    k = 3
+    G = n_int * k
+    rho = np.zeros((G, G))
+    mx = np.zeros((G, G))
+    for i in range(n):
+        wx = oracle.lagrange(k, (xy[i, 0] - lo) / h - bx[i])
+        wy = oracle.lagrange(k, (xy[i, 1] - lo) / h - by[i])
+        for ly in range(k):
+            for lx in range(k):
+                qy, qx = by[i] * k + ly, bx[i] * k + lx
+                rho[qy, qx] += wx[lx] * wy[ly]
+                mx[qy, qx] += wx[lx] * wy[ly] * (xy[i, 0] - (lo + (qx + 0.5) * h / k))
+    assert rel_l2(charges[0], rho) < 1e-5
+    assert rel_l2(charges[1], mx) < 1e-5
+
+
+def test_fft_short_layout_matches_oracle(tfdp):
+    rng = np.random.default_rng(12)
+    n = 20000
+    e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
+    xy = rng.uniform(-70, 70, size=(n, 2)).astype(np.float32)
+    T = 10
+    p = _params(tfdp, grid_max=255, total_iters=300)
+    with tfdp.Graph(n, e, xy, p) as g:
+        g.iterate(T)
+        out = g.get_positions()
+        assert g.stats()["device_flags"] == 0
+    ref = oracle.iterate(xy.astype(np.float64), e, T, mode="fft", k=3, grid_max=255,
+                         policy=oracle.GRID_SNAP_H, P=512, T=300)
+    assert rel_l2(out, ref) <= POS_TOL, rel_l2(out, ref)
+
+
+def test_respectrum_only_when_kernel_parameters_change(tfdp):
+    rng = np.random.default_rng(4)
+    n = 4000
+    e = synth.erdos_renyi(n, 8000, rng)
+    xy = rng.uniform(-100, 100, size=(n, 2)).astype(np.float32)
+    with tfdp.Graph(n, e, xy, _params(tfdp, grid_max=255)) as g:
+        g.eval_forces()
+        b0 = g.stats()["spectrum_builds"]
+        g.eval_forces()
+        assert g.stats()["spectrum_builds"] == b0  # same positions: cached
+        g.set_params(alpha=0.05, beta=12.0)       # edge term only
+        g.eval_forces()
+        assert g.stats()["spectrum_builds"] == b0
+        g.set_params(gamma=4.0)                   # kernel changes
+        fr, fa = g.eval_forces()
+        st = g.stats()
+        assert st["spectrum_builds"] == b0 + 1
+    _, ref = _oracle_fft(xy, st, 4.0, 3, 255, 1)
+    assert rel_l2(fr, ref) <= FORCE_TOL
+    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.05, 12.0)) <= FORCE_TOL
+
+
+# ------------------------------------------------------------------ edge cases
+
+def test_degenerate_graphs(tfdp):
+    # no nodes
+    with tfdp.Graph(0, np.zeros((0, 2), np.int32), np.zeros((0, 2), np.float32)) as g:
+        g.iterate(3)
+        assert g.get_positions().shape == (0, 2)
+    # one node, no edges: no force, no motion
+    with tfdp.Graph(1, np.zeros((0, 2), np.int32), np.array([[3.0, -2.0]], np.float32)) as g:
+        fr, fa = g.eval_forces()
+        assert np.all(fr == 0) and np.all(fa == 0)
+        g.iterate(5)
+        assert np.array_equal(g.get_positions(), [[3.0, -2.0]])
+    # all nodes at one point: the layout square is widened, forces vanish
+    xy = np.full((50, 2), 7.5, np.float32)
+    with tfdp.Graph(50, np.zeros((0, 2), np.int32), xy) as g:
+        fr, _ = g.eval_forces()
+        assert np.abs(fr).max() < 1e-6
+        assert g.stats()["device_flags"] == 0
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_two_connected_nodes_reach_equilibrium(tfdp, mode):
+    dstar = 0.31467370  # closed form at alpha=0.1, beta=8, gamma=2
+    xy = np.array([[0.0, 0.0], [1.3, 0.4]], np.float32)
+    p = _params(tfdp, rep_mode=mode, total_iters=300, grid_max=255)
+    with tfdp.Graph(2, [[0, 1]], xy, p) as g:
+        g.iterate(300)
+        out = g.get_positions()
+    d = np.linalg.norm(out[0] - out[1])
+    if mode == 0:
+        assert abs(d - dstar) < 1e-5
+    else:
+        # ibFFT: the interpolated kernel shifts the balance point; compare with the oracle
+        ref = oracle.iterate(xy.astype(np.float64), [[0, 1]], 300, mode="fft", grid_max=255,
+                             P=512, T=300)
+        assert abs(d - np.linalg.norm(ref[0] - ref[1])) < 1e-4
+
+
+def test_set_positions_and_iteration_counter(tfdp):
+    rng = np.random.default_rng(8)
+    n = 1000
+    e = synth.erdos_renyi(n, 3000, rng)
+    xy = rng.uniform(-20, 20, size=(n, 2)).astype(np.float32)
+    p = _params(tfdp, grid_max=255, total_iters=50)
+    with tfdp.Graph(n, e, xy, p) as g:
+        g.iterate(7)
+        a = g.get_positions()
+        g.set_positions(xy)
+        g.set_iteration(0)
+        g.iterate(7)
+        b = g.get_positions()
+        assert np.array_equal(a, b)  # same start, same schedule: deterministic replay
+        g.iterate(3)  # odd count: buffer parity changes
+        c = g.get_positions()
+        g.set_positions(a)
+        g.set_iteration(7)
+        g.iterate(3)
+        np.testing.assert_array_equal(g.get_positions(), c)
