@@ -309,7 +309,11 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
     const NodeLaunch a = g->node_launch();
     const bool tm = g->timing;
     int mark_i = 0;
-    auto mark = [&]() -> cudaError_t { return tm ? cudaEventRecord(g->ev[mark_i++], s) : cudaSuccess; };
+    // cudaEventRecordExternal makes the record a node of a captured graph (a plain
+    // record inside a capture only orders the capture and is never timed)
+    auto mark = [&]() -> cudaError_t {
+        return tm ? cudaEventRecordWithFlags(g->ev[mark_i++], s, cudaEventRecordExternal) : cudaSuccess;
+    };
     CK(mark());
     if (g->params.rep_mode == TFDP_REP_EXACT) {
         CK(launch_exact_pairs(a, advance, s));
