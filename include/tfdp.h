@@ -199,6 +199,32 @@ tfdp_status tfdp_synchronize(tfdp_graph* g);
 tfdp_status tfdp_destroy_graph(tfdp_graph* g);
 
 /*
+ * Exact repulsion without any device allocation, for callers that cannot allocate:
+ * code running under a framework whose caching allocator owns the device memory pool
+ * and forbids side allocations, and latency-critical loops where cudaMalloc / cudaFree
+ * could synchronise the device. The paper has no counterpart of this entry point; its
+ * arithmetic is the exact sum of Sec. 3.4 Eq. (repfK):
+ *     frep(i) = sum_{j != i} (x_i - x_j) / (1 + |x_i - x_j|^2)^gamma.
+ *   xy      device pointer, n x 2 FP32 positions (caller-owned, read only)
+ *   n       0 <= n <= TFDP_NOALLOC_MAX_N, else TFDP_ERR_PARAM_RANGE
+ *   gamma   > 1, else TFDP_ERR_PARAM_RANGE
+ *   frep    device pointer, n x 2 FP32 output (caller-owned)
+ *   stream  cudaStream_t the two kernels are enqueued on (NULL = legacy default);
+ *           the call returns once they are enqueued
+ * Its only scratch is a fixed 2 MiB array of partial sums inside the library; every
+ * GPU that loads the library holds it until the process exits. The call makes no
+ * cudaMalloc, cudaFree or other allocating call. The first call on a device does a
+ * one-time set-up (it looks up the device address of that array with the device
+ * current); make that first call before any stream capture on the device. All calls
+ * share the array: calls that can overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other's results, so order them (one stream, or
+ * events). Each call overwrites every entry it reads, so no clearing is needed.
+ */
+#define TFDP_NOALLOC_MAX_N 16384
+tfdp_status tfdp_exact_repulsion_noalloc(const float* xy, int64_t n, double gamma, float* frep,
+                                         void* stream);
+
+/*
  * Test hook: copy an internal buffer of the last FFT-mode force evaluation to host
  * memory `dst` of `bytes` bytes (TFDP_ERR_INVALID_ARG if too small or unknown).
  *   TFDP_DEBUG_GRID_CHARGES  3 x G x G FP32: rho, m_x, m_y (the spread, Sec. 3.4 step 1)

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtfdp.so")
-SOURCES = ["tfdp_api.cu", "node_kernels.cu", "fft_kernels.cu"]
+SOURCES = ["tfdp_api.cu", "node_kernels.cu", "fft_kernels.cu", "noalloc.cu"]
 HEADERS = ["common.cuh", "fft.cuh", "launch.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

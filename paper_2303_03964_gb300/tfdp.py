@@ -79,7 +79,10 @@ _SIGS = {
     "tfdp_get_stage_times": ([_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
     "tfdp_destroy_graph": ([_p], ctypes.c_int),
     "tfdp_debug_fetch": ([_p, ctypes.c_int, _p, ctypes.c_size_t], ctypes.c_int),
+    "tfdp_exact_repulsion_noalloc": ([_p, ctypes.c_int64, ctypes.c_double, _p, _p], ctypes.c_int),
 }
+
+NOALLOC_MAX_N = 16384
 
 
 def _load():
@@ -244,3 +247,22 @@ class Graph:
         _check(lib.tfdp_debug_fetch(self._h, int(what), a.ctypes.data_as(_p), a.nbytes),
                "tfdp_debug_fetch")
         return a
+
+
+def exact_repulsion_noalloc(xy, frep, gamma=2.0, stream=0):
+    """Exact repulsion into a caller-owned CUDA tensor without any device allocation.
+
+    For callers that cannot allocate device memory (a framework's caching allocator
+    owns the pool, or a latency-critical loop must not risk cudaMalloc / cudaFree
+    synchronising the device). ``xy`` and ``frep`` are contiguous float32 CUDA tensors
+    of shape (n, 2), n <= NOALLOC_MAX_N. Asynchronous on ``stream``. All calls share one
+    fixed scratch array in the library: calls that may overlap on the GPU race.
+    """
+    if not (_is_torch_cuda(xy) and _is_torch_cuda(frep)):
+        raise TypeError("xy and frep must be CUDA tensors")
+    assert xy.is_contiguous() and frep.is_contiguous() and xy.numel() == frep.numel()
+    n = xy.numel() // 2
+    _check(lib.tfdp_exact_repulsion_noalloc(_p(xy.data_ptr()), n, float(gamma),
+                                            _p(frep.data_ptr()), _p(stream or 0)),
+           "tfdp_exact_repulsion_noalloc")
+    return frep
