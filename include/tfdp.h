@@ -106,13 +106,13 @@ typedef struct {
 
 /* Stages of one iteration, in launch order, for tfdp_get_stage_times. */
 enum {
-    TFDP_STAGE_SORT = 0,          /* FFT path: box of each node, counting sort (5 kernels) */
+    TFDP_STAGE_SORT = 0,          /* FFT path: grid policy, box of each node, counting sort (6 kernels) */
     TFDP_STAGE_SPREAD = 1,        /* FFT path: Lagrange projection onto the grid */
     TFDP_STAGE_SPECTRUM = 2,      /* FFT path: kernel spectrum (returns at once when cached) */
     TFDP_STAGE_ROWS_FWD = 3,      /* FFT path: forward transform along x */
     TFDP_STAGE_COLS = 4,          /* FFT path: transform along y, spectral product, inverse */
     TFDP_STAGE_ROWS_INV = 5,      /* FFT path: inverse transform along x */
-    TFDP_STAGE_GATHER_UPDATE = 6, /* FFT path: back-projection + attraction + update */
+    TFDP_STAGE_GATHER_UPDATE = 6, /* FFT path: back-projection, then attraction + update (2 kernels) */
     TFDP_STAGE_EXACT = 7,         /* exact path: all-pairs repulsion */
     TFDP_STAGE_EDGE_UPDATE = 8,   /* exact path: attraction + update */
     TFDP_NUM_STAGES = 9

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtfdp.so")
 SOURCES = ["tfdp_api.cu", "node_kernels.cu", "fft_kernels.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "fft.cuh", "launch.h"]
+HEADERS = ["common.cuh", "fft.cuh", "fft_reg.cuh", "launch.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2"]

@@ -36,6 +36,7 @@ struct DevParams {
     int P;           // FFT size per axis
     int log2P;
     int gamma_int;   // gamma if it is a small integer (2..8), else 0
+    const double* step_table;  // s_t for t = 0 .. total_iters - 1 (host-computed, FP64)
 };
 
 // Grid of one iteration, Sec. 3.4: square [lo, lo + N_int h]^2, N_int x N_int boxes,
@@ -46,6 +47,8 @@ struct GridDesc {
     double L;       // layout square side (after the floor)
     float lo_f;     // lo as FP32 (exact)
     float h_f;      // h rounded to FP32 (used by the box decision)
+    float h_lo_f;   // h - h_f rounded to FP32 (h = h_f + h_lo_f to ~2^-48 relative)
+    float hk_f;     // h / k rounded to FP32 (grid spacing)
     int n_int;
     int G;
 };
@@ -107,7 +110,7 @@ __device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevP
         double base = ldexp(1.0, e - 1);
         h = ldexp(1.0, e);
         for (int j = 0; j <= 16; ++j) {
-            double cand = base * (16.0 + (double)j) / 16.0;
+            double cand = base * (16.0 + (double)j) * 0.0625;  // exact
             if ((double)n_int * cand >= L) { h = cand; break; }
         }
     }
@@ -116,6 +119,8 @@ __device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevP
     g.L = L;
     g.lo_f = lo_f;
     g.h_f = __double2float_rn(h);
+    g.h_lo_f = __double2float_rn(h - (double)g.h_f);
+    g.hk_f = __double2float_rn(h / (double)p.k);
     g.n_int = n_int;
     g.G = n_int * p.k;
     return g;
@@ -149,11 +154,12 @@ __device__ __forceinline__ void lagrange(float u, float* w) {
     }
 }
 
-// Step size of iteration t: s0 (s_min / s0)^(t / (T - 1)) (reading; the paper gives none).
+// Step size of iteration t: s0 (s_min / s0)^(t / (T - 1)) (reading; the paper gives none),
+// read from a table the host fills in FP64, clamped at t = T - 1.
 __device__ __forceinline__ double step_size(long long t, const DevParams& p) {
-    if (p.total_iters <= 1) return p.step0;
     if (t > p.total_iters - 1) t = p.total_iters - 1;
-    return p.step0 * pow(p.step_min / p.step0, (double)t / (double)(p.total_iters - 1));
+    if (t < 0) t = 0;
+    return p.step_table[t];
 }
 
 // ---------------------------------------------------------------- reductions

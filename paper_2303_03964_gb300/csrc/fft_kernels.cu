@@ -25,6 +25,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "fft_reg.cuh"
 #include "launch.h"
 
 namespace tfdp {
@@ -50,31 +51,34 @@ struct GridSource {
 // kernels exactly odd (their spectra exactly imaginary).
 struct KernelSource {
     int P;
-    double s, gamma;
+    float s2, s, gamma;  // spacing^2, spacing, exponent (FP32)
+    int gamma_int;
     __device__ __forceinline__ void bind(const DevState* st, const DevParams* prm) {
-        s = st->grid.h / (double)prm->k;
-        gamma = prm->gamma;
+        const double sd = st->grid.h / (double)prm->k;
+        s = (float)sd;
+        s2 = (float)(sd * sd);
+        gamma = (float)prm->gamma;
         gamma_int = prm->gamma_int;
     }
     __device__ __forceinline__ int rows(const DevState*) const { return P; }
     __device__ __forceinline__ bool active(const DevState* st) const { return st->spec_dirty != 0; }
-    int gamma_int;
     __device__ __forceinline__ float operator()(int c, int y, int x, int) const {
         const int half = P >> 1;
         if (x == half || y == half) return 0.0f;
         const int dx = (x < half) ? x : x - P;
         const int dy = (y < half) ? y : y - P;
-        const double u = 1.0 + ((double)dx * dx + (double)dy * dy) * s * s;
-        double K;
+        // dx^2 + dy^2 < 2^24 is exact in FP32
+        const float u = fmaf((float)(dx * dx + dy * dy), s2, 1.0f);
+        float K;
         if (gamma_int > 0) {  // integer gamma: u^-gamma by multiplication
-            double ug = u;
+            float ug = u;
             for (int q = 1; q < gamma_int; ++q) ug *= u;
-            K = 1.0 / ug;
+            K = 1.0f / ug;
         } else {
-            K = pow(u, -gamma);
+            K = powf(u, -gamma);
         }
-        if (c == 0) return (float)K;
-        return (float)((c == 1 ? (double)dx : (double)dy) * s * K);
+        if (c == 0) return K;
+        return (float)(c == 1 ? dx : dy) * s * K;
     }
 };
 
@@ -265,6 +269,167 @@ __global__ void __launch_bounds__(256) k_rows_inv(const float2* __restrict__ T2,
     }
 }
 
+// ---------------------------------------------------------------- register-resident path
+// Same transforms as k_rows_fwd / k_cols / k_rows_inv, with each thread holding eight
+// values of each of its three sequences (fft_reg.cuh). RG row pairs (or columns) per
+// CTA, T = P/8 threads each.
+template <int LOGP>
+struct RegGeom {
+    static constexpr int P = 1 << LOGP;
+    static constexpr int T = P / 8;
+    static constexpr int RG = (T >= 256) ? 1 : 256 / T;   // row pairs per CTA (rows kernels), <= 16
+    static constexpr int CG = (T >= 256) ? 1 : 256 / T;   // columns per CTA (column kernel)
+    static constexpr size_t rows_smem = (size_t)RG * 3 * P * sizeof(float2);
+    static constexpr size_t cols_smem = (size_t)CG * 3 * P * sizeof(float2);
+};
+
+template <int LOGP, class Src>
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
+    k_rows_fwd_r(Src src, float2* __restrict__ T1, int ystride, const float2* __restrict__ tw,
+                 const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    extern __shared__ float2 sm[];
+    if (!src.active(st)) return;
+    src.bind(st, prm);
+    const int G = src.rows(st);
+    const int ybase = blockIdx.x * (2 * RG);
+    if (ybase >= G) return;
+    const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
+    const int y0 = ybase + 2 * lr;
+    float2* smr = sm + (size_t)lr * 3 * P;
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int x = t + r * T;
+            v[c][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+        }
+    reg_fft_forward<LOGP, 3>(v, smr, tw, t);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) smr[c * P + swz(8 * t + r)] = v[c][r];
+    __syncthreads();
+    // split Z = FFT(a + i b) into FFT(a), FFT(b); one thread per (channel, kx) writes
+    // 2 RG consecutive rows (RG row pairs) of T1[c][kx][.]
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = idx - c * NH;
+        const int pk = swz(pos_of_freq<LOGP>(kx));
+        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+        float4* dst = reinterpret_cast<float4*>(T1 + ((size_t)c * NH + kx) * ystride + ybase);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float2* seq = sm + ((size_t)q * 3 + c) * P;
+            const float2 Z = seq[pk], W = seq[pn];
+            dst[q] = make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+        }
+    }
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG)
+    k_cols_r(const float2* __restrict__ T1, float2* __restrict__ T2, int ystride, const float* __restrict__ specK,
+             const float* __restrict__ specHx, const float* __restrict__ specHy, const float2* __restrict__ tw,
+             const DevState* __restrict__ st) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
+    extern __shared__ float2 sm[];
+    const int lc = threadIdx.x / T, t = threadIdx.x - lc * T;
+    const int kx = blockIdx.x * Gm::CG + lc;
+    const bool valid = kx < NH;
+    const int G = st->grid.G;
+    float2* smc = sm + (size_t)lc * 3 * P;
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = t + r * T;
+            v[c][r] = (valid && y < G) ? T1[((size_t)c * NH + kx) * ystride + y] : make_float2(0.f, 0.f);
+        }
+    reg_fft_forward<LOGP, 3>(v, smc, tw, t);
+    if (valid) {
+        const size_t so = (size_t)kx * P + 8 * t;
+        const float4* pK = reinterpret_cast<const float4*>(specK + so);
+        const float4* pX = reinterpret_cast<const float4*>(specHx + so);
+        const float4* pY = reinterpret_cast<const float4*>(specHy + so);
+        float K[8], hx[8], hy[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 a = __ldg(pK + h), b = __ldg(pX + h), d = __ldg(pY + h);
+            K[4 * h] = a.x; K[4 * h + 1] = a.y; K[4 * h + 2] = a.z; K[4 * h + 3] = a.w;
+            hx[4 * h] = b.x; hx[4 * h + 1] = b.y; hx[4 * h + 2] = b.z; hx[4 * h + 3] = b.w;
+            hy[4 * h] = d.x; hy[4 * h + 1] = d.y; hy[4 * h + 2] = d.z; hy[4 * h + 3] = d.w;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float2 rr = v[0][r], mx = v[1][r], my = v[2][r];
+            v[0][r] = make_float2(K[r] * rr.x, K[r] * rr.y);
+            v[1][r] = make_float2(-hx[r] * rr.y - K[r] * mx.x, hx[r] * rr.x - K[r] * mx.y);
+            v[2][r] = make_float2(-hy[r] * rr.y - K[r] * my.x, hy[r] * rr.x - K[r] * my.y);
+        }
+    }
+    reg_fft_inverse<LOGP, 3>(v, smc, tw, t);
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int y = t + r * T;
+                if (y < G) T2[((size_t)c * NH + kx) * ystride + y] = v[c][r];
+            }
+    }
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
+    k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
+                 const float2* __restrict__ tw, const DevState* __restrict__ st) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    extern __shared__ float2 sm[];
+    const int G = st->grid.G;
+    const int ybase = blockIdx.x * (2 * RG);
+    if (ybase >= G) return;
+    // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = idx - c * NH;
+        const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
+        const int pk = swz(pos_of_freq<LOGP>(kx));
+        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const int y = ybase + 2 * q;
+            float4 X = (y < G) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (y + 1 >= G) { X.z = 0.f; X.w = 0.f; }  // row past G: never written
+            float2* seq = sm + ((size_t)q * 3 + c) * P;
+            seq[pk] = make_float2(X.x - X.w, X.y + X.z);
+            if (kx != 0 && kx != P / 2) seq[pn] = make_float2(X.x + X.w, X.z - X.y);
+        }
+    }
+    __syncthreads();
+    const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
+    const int y0 = ybase + 2 * lr;
+    float2* smr = sm + (size_t)lr * 3 * P;
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[c][r] = smr[c * P + swz(8 * t + r)];
+    reg_fft_inverse<LOGP, 3>(v, smr, tw, t);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int x = t + r * T;
+        if (x >= G) continue;
+        if (y0 < G) gout[(size_t)y0 * Gs + x] = make_float4(v[0][r].x, v[1][r].x, v[2][r].x, 0.0f);
+        if (y0 + 1 < G) gout[(size_t)(y0 + 1) * Gs + x] = make_float4(v[0][r].y, v[1][r].y, v[2][r].y, 0.0f);
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 template <int LOGP>
 struct FftGeom {
@@ -274,6 +439,8 @@ struct FftGeom {
     static constexpr size_t rows_smem = (size_t)3 * RPC / 2 * padded_len(P) * sizeof(float2);
     static constexpr size_t cols_smem = (size_t)3 * padded_len(P) * sizeof(float2);
 };
+
+constexpr int kMaxRegLogP = 12;  // register-resident path up to P = 4096
 
 template <int LOGP>
 static cudaError_t set_attrs() {
@@ -285,7 +452,15 @@ static cudaError_t set_attrs() {
     if ((e = cudaFuncSetAttribute(k_rows_fwd<LOGP, RPC, KernelSource>, A, (int)Gm::rows_smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_rows_inv<LOGP, RPC>, A, (int)Gm::rows_smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_cols<LOGP>, A, (int)Gm::cols_smem)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_spec_cols<LOGP>, A, (int)Gm::cols_smem);
+    if ((e = cudaFuncSetAttribute(k_spec_cols<LOGP>, A, (int)Gm::cols_smem)) != cudaSuccess) return e;
+    if (LOGP <= kMaxRegLogP) {
+        using Rg = RegGeom<(LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP)>;
+        constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
+        if ((e = cudaFuncSetAttribute(k_rows_fwd_r<L, GridSource>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_cols_r<L>, A, (int)Rg::cols_smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_rows_inv_r<L>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <int LOGP>
@@ -315,8 +490,9 @@ static cudaError_t launch_spectrum_impl(const FftLaunch& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     KernelSource ks;
     ks.P = P;
-    ks.s = 0.0;
-    ks.gamma = 0.0;
+    ks.s = 0.0f;
+    ks.s2 = 0.0f;
+    ks.gamma = 0.0f;
     ks.gamma_int = 0;
     k_rows_fwd<LOGP, Gm::RPC, KernelSource><<<P / Gm::RPC, 256, Gm::rows_smem, s>>>(ks, a.S1, P, a.tw, a.st, a.prm);
     k_spec_cols<LOGP><<<P / 2 + 1, 256, Gm::cols_smem, s>>>(a.S1, a.specK, a.specHx, a.specHy, a.tw, a.st);
@@ -331,6 +507,13 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
     GridSource gs;
     gs.gin = a.gin;
     gs.Gs = a.Gs;
+    if (LOGP <= kMaxRegLogP) {
+        constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
+        using Rg = RegGeom<L>;
+        const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+        k_rows_fwd_r<L, GridSource><<<blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(gs, a.T1, a.ystride, a.tw, a.st, a.prm);
+        return cudaGetLastError();
+    }
     const int row_blocks = (a.G_max + Gm::RPC - 1) / Gm::RPC;
     k_rows_fwd<LOGP, Gm::RPC, GridSource><<<row_blocks, 256, Gm::rows_smem, s>>>(gs, a.T1, a.ystride, a.tw, a.st, a.prm);
     return cudaGetLastError();
@@ -342,6 +525,13 @@ static cudaError_t launch_cols_impl(const FftLaunch& a, cudaStream_t s) {
     constexpr int P = Gm::P;
     cudaError_t e = ensure_attrs<LOGP>();
     if (e != cudaSuccess) return e;
+    if (LOGP <= kMaxRegLogP) {
+        constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
+        using Rg = RegGeom<L>;
+        const int blocks = (P / 2 + 1 + Rg::CG - 1) / Rg::CG;
+        k_cols_r<L><<<blocks, Rg::T * Rg::CG, Rg::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy, a.tw, a.st);
+        return cudaGetLastError();
+    }
     k_cols<LOGP><<<P / 2 + 1, 256, Gm::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy, a.tw, a.st);
     return cudaGetLastError();
 }
@@ -351,6 +541,13 @@ static cudaError_t launch_rows_inv_impl(const FftLaunch& a, cudaStream_t s) {
     using Gm = FftGeom<LOGP>;
     cudaError_t e = ensure_attrs<LOGP>();
     if (e != cudaSuccess) return e;
+    if (LOGP <= kMaxRegLogP) {
+        constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
+        using Rg = RegGeom<L>;
+        const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+        k_rows_inv_r<L><<<blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(a.T2, a.ystride, a.gout, a.Gs, a.tw, a.st);
+        return cudaGetLastError();
+    }
     const int row_blocks = (a.G_max + Gm::RPC - 1) / Gm::RPC;
     k_rows_inv<LOGP, Gm::RPC><<<row_blocks, 256, Gm::rows_smem, s>>>(a.T2, a.ystride, a.gout, a.Gs, a.tw, a.st);
     return cudaGetLastError();

@@ -14,7 +14,7 @@ struct FftLaunch {
     int logP;            // FFT size P = 2^logP per axis (7..13)
     int G_max;           // largest grid G this graph may use
     int Gs;              // row stride (and rows per plane) of gin / gout
-    int ystride;         // column stride of T1 / T2 (multiple of 4, >= G_max)
+    int ystride;         // column stride of T1 / T2 (multiple of 32, >= G_max)
     const float* gin;    // 3 planes of Gs x Gs: rho, m^x, m^y
     float2* T1;          // [3][P/2+1][ystride]
     float2* T2;          // [3][P/2+1][ystride]

@@ -1,16 +1,17 @@
 // node_kernels.cu -- per-node stages of one t-FDP iteration (arXiv 2303.03964).
 //
 //   k_bbox           layout square extremes (Sec. 3.4: [x_min, x_max]^2 over both axes)
+//   k_grid           grid policy of the iteration (Sec. 3.4 "Choices of k"), one thread
 //   k_bin            box of every node (Sec. 3.4: "projecting each data point into the
 //                    corresponding grid square"), counting-sort histogram
 //   k_scan_*         exclusive scan of the box counts
 //   k_scatter        cell-sorted copy of the positions
 //   k_spread         Lagrange projection onto the k x k nodes of each box (Sec. 3.4,
 //                    step 1): rho, m^x, m^y; one thread owns one box, so no atomics
-//   k_gather_update  back-projection (step 3), attraction over the CSR (Eq. newforce),
-//                    capped step (update)
+//   k_gather_sorted  back-projection (step 3) in cell-sorted order
 //   k_exact          tiled all-pairs repulsion (Eq. repfK), FP32
-//   k_edge_update    attraction + update for the exact path
+//   k_edge_update    attraction over the CSR (Eq. newforce) + capped step (update),
+//                    on the repulsion of either path
 //
 // Node coordinates relative to their box origin are formed exactly (TwoSum and an
 // FMA-exact product), so that FP32 coordinates of magnitude |x| ~ 10^3 keep the
@@ -36,12 +37,12 @@ struct AxisGeom {
     int n_int;
 };
 
-__device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g, int K) {
+__device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g) {
     AxisGeom a;
     a.lo = g.lo_f;
     a.h_hi = g.h_f;
-    a.h_lo = (float)(g.h - (double)g.h_f);
-    a.hk = (float)(g.h / (double)K);
+    a.h_lo = g.h_lo_f;
+    a.hk = g.hk_f;
     a.n_int = g.n_int;
     return a;
 }
@@ -69,14 +70,21 @@ struct BlockAcc {
     double fx, fy;
 };
 
+__device__ __forceinline__ float warp_sumf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // Reduce (min, max, sum fx, sum fy) over the block; thread 0 publishes with atomics.
-__device__ void block_publish(BlockAcc v, DevState* st, int slot, bool bbox) {
+// The force sums are FP32 within a warp (one node per thread) and FP64 above.
+__device__ void block_publish(float mn, float mx, float fx, float fy, DevState* st, int slot, bool bbox) {
     __shared__ float s_mn[32], s_mx[32];
     __shared__ double s_fx[32], s_fy[32];
-    v.mn = warp_min(v.mn);
-    v.mx = warp_max(v.mx);
-    v.fx = warp_sum(v.fx);
-    v.fy = warp_sum(v.fy);
+    BlockAcc v;
+    v.mn = warp_min(mn);
+    v.mx = warp_max(mx);
+    v.fx = (double)warp_sumf(fx);
+    v.fy = (double)warp_sumf(fy);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) { s_mn[w] = v.mn; s_mx[w] = v.mx; s_fx[w] = v.fx; s_fy[w] = v.fy; }
     __syncthreads();
@@ -130,15 +138,38 @@ __global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict_
 
 // ---------------------------------------------------------------- attraction + update
 // alpha * sum_{j <-> i} (1 + beta / (1 + d^2)) (x_j - x_i), Eq. (newforce).
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
                                              const int* __restrict__ col, const float2* __restrict__ xy,
                                              float alpha, float beta) {
     float fx = 0.0f, fy = 0.0f;
+    int e = rowptr[i];
     const int e1 = rowptr[i + 1];
-    for (int e = rowptr[i]; e < e1; ++e) {
+    // four neighbours per round so that their loads are in flight together
+    for (; e + 4 <= e1; e += 4) {
+        int j[4];
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float dx = q[u].x - p.x, dy = q[u].y - p.y;
+            const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            fx = fmaf(c, dx, fx);
+            fy = fmaf(c, dy, fy);
+        }
+    }
+    for (; e < e1; ++e) {
         const float2 q = xy[__ldg(col + e)];
         const float dx = q.x - p.x, dy = q.y - p.y;
-        const float c = 1.0f + beta / (1.0f + (dx * dx + dy * dy));
+        const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
         fx = fmaf(c, dx, fx);
         fy = fmaf(c, dy, fy);
     }
@@ -147,49 +178,56 @@ __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restr
 
 // x + D min(1, s / |D|)
 __device__ __forceinline__ float2 capped_step(float2 p, float2 D, float s) {
-    const float nrm = sqrtf(D.x * D.x + D.y * D.y);
-    const float c = (nrm > s) ? s / nrm : 1.0f;
-    return make_float2(p.x + c * D.x, p.y + c * D.y);
+    const float d2 = D.x * D.x + D.y * D.y;
+    const float c = (d2 > s * s) ? s * rsqrtf(d2) : 1.0f;
+    return make_float2(fmaf(c, D.x, p.x), fmaf(c, D.y, p.y));
 }
 
-// ---------------------------------------------------------------- FFT path: bin
-template <int K>
-__global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a, int advance) {
+// ---------------------------------------------------------------- FFT path: grid
+// One thread: the grid of this iteration from the layout extremes (exact FP64
+// decisions), the step s_t, the spectrum key, and the bookkeeping of the iteration.
+__global__ void k_grid(NodeLaunch a, int advance) {
+    if (threadIdx.x != 0) return;
     DevState* st = a.st;
+    const DevParams prm = *a.prm;
     const long long t = st->iter;
     const int cur = (int)(t & 1);
-    const float2* __restrict__ xy = a.xy[cur];
-    const float lo = ord2f(st->bbox[cur][0]), hi = ord2f(st->bbox[cur][1]);
-    const DevParams prm = *a.prm;
-    const GridDesc g = make_grid(lo, hi, prm);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->grid = g;
-        st->t_cur = t;
-        st->step_cur = step_size(t, prm);
-        st->net_frep[0] = 0.0;
-        st->net_frep[1] = 0.0;
-        if (advance) {
-            st->bbox[cur ^ 1][0] = kOrdMinInit;
-            st->bbox[cur ^ 1][1] = kOrdMaxInit;
-        }
-        const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
-                           st->spec_k == prm.k && st->spec_P == prm.P;
-        st->spec_dirty = valid ? 0 : 1;
-        if (!valid) {
-            st->spec_h = g.h;
-            st->spec_gamma = prm.gamma;
-            st->spec_k = prm.k;
-            st->spec_P = prm.P;
-            st->spec_valid = 1;
-            st->spec_builds += 1;
-        }
+    const GridDesc g = make_grid(ord2f(st->bbox[cur][0]), ord2f(st->bbox[cur][1]), prm);
+    st->grid = g;
+    st->t_cur = t;
+    st->step_cur = step_size(t, prm);
+    st->net_frep[0] = 0.0;
+    st->net_frep[1] = 0.0;
+    if (advance) {
+        st->bbox[cur ^ 1][0] = kOrdMinInit;
+        st->bbox[cur ^ 1][1] = kOrdMaxInit;
     }
+    const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
+                       st->spec_k == prm.k && st->spec_P == prm.P;
+    st->spec_dirty = valid ? 0 : 1;
+    if (!valid) {
+        st->spec_h = g.h;
+        st->spec_gamma = prm.gamma;
+        st->spec_k = prm.k;
+        st->spec_P = prm.P;
+        st->spec_valid = 1;
+        st->spec_builds += 1;
+    }
+}
+
+// Box of every node (the FP32 decision) and its slot in the box (counting-sort histogram).
+__global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a) {
+    const DevState* st = a.st;
+    const int cur = (int)(st->t_cur & 1);
+    const float2* __restrict__ xy = a.xy[cur];
+    const float lo = st->grid.lo_f, h = st->grid.h_f;
+    const int n_int = st->grid.n_int;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         const float2 p = xy[i];
         float tq;
-        const int bx = box_of(p.x, g.lo_f, g.h_f, g.n_int, &tq);
-        const int by = box_of(p.y, g.lo_f, g.h_f, g.n_int, &tq);
-        const int key = by * g.n_int + bx;
+        const int bx = box_of(p.x, lo, h, n_int, &tq);
+        const int by = box_of(p.y, lo, h, n_int, &tq);
+        const int key = by * n_int + bx;
         const int slot = atomicAdd(a.cnt + key, 1);
         a.keyslot[i] = make_int2(key, slot);
     }
@@ -303,7 +341,7 @@ template <int K>
 __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
     const GridDesc g = a.st->grid;
     const int nbox = g.n_int * g.n_int;
-    const AxisGeom ag = axis_geom(g, K);
+    const AxisGeom ag = axis_geom(g);
     const size_t plane = (size_t)a.Gs * a.Gs;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
         const int by = b / g.n_int;
@@ -351,23 +389,17 @@ __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
 }
 
 // ---------------------------------------------------------------- FFT path: gather
-// frep(i) = sum_p w_ip [ (x_i - y_p) A_p + O_p ]  (well-conditioned Eq. Fr1/Fr2),
-// then attraction and the capped step (EVAL = false) or outputs (EVAL = true).
-template <int K, bool EVAL>
-__global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a) {
-    DevState* st = a.st;
-    const long long t = st->t_cur;
-    const int cur = (int)(t & 1);
-    const float2* __restrict__ xin = a.xy[cur];
-    float2* __restrict__ xout = a.xy[cur ^ 1];
-    const GridDesc g = st->grid;
-    const AxisGeom ag = axis_geom(g, K);
-    const float step = (float)st->step_cur;
-    const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
-    BlockAcc acc{INFINITY, -INFINITY, 0.0, 0.0};
-    unsigned bad = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const float2 p = xin[i];
+// frep(i) = sum_p w_ip [ (x_i - y_p) A_p + O_p ]  (well-conditioned Eq. Fr1/Fr2).
+// Nodes are visited in cell-sorted order, so neighbouring threads read the same grid
+// values; the result goes to the node's caller-order slot. Attraction and the update
+// follow in k_edge_update (caller order), which reads these values.
+template <int K>
+__global__ void __launch_bounds__(kNodeThreads) k_gather_sorted(NodeLaunch a, float2* __restrict__ frep) {
+    const GridDesc g = a.st->grid;
+    const AxisGeom ag = axis_geom(g);
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
+        const float2 p = a.sxy[s];
+        const int i = a.perm[s];
         float ox, oy;
         const int bx = box_offset(p.x, ag, &ox);
         const int by = box_offset(p.y, ag, &oy);
@@ -391,22 +423,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a) {
                 fry = fmaf(w, fmaf(dy[ly], v.x, v.z), fry);
             }
         }
-        const float2 fa = attraction(i, p, a.rowptr, a.col, xin, alpha, beta);
-        acc.fx += (double)frx;
-        acc.fy += (double)fry;
-        if (EVAL) {
-            a.frep_out[i] = make_float2(frx, fry);
-            a.fatt_out[i] = fa;
-        } else {
-            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
-            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
-            xout[i] = q;
-            acc.mn = fminf(acc.mn, fminf(q.x, q.y));
-            acc.mx = fmaxf(acc.mx, fmaxf(q.x, q.y));
-        }
+        frep[i] = make_float2(frx, fry);
     }
-    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
-    block_publish(acc, st, cur ^ 1, !EVAL);
 }
 
 // ---------------------------------------------------------------- exact path
@@ -502,7 +520,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
     float2* __restrict__ xout = a.xy[cur ^ 1];
     const float step = (float)st->step_cur;
     const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
-    BlockAcc acc{INFINITY, -INFINITY, 0.0, 0.0};
+    float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
     unsigned bad = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
         float frx = 0.0f, fry = 0.0f;
@@ -513,8 +531,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
         }
         const float2 p = xin[i];
         const float2 fa = attraction(i, p, a.rowptr, a.col, xin, alpha, beta);
-        acc.fx += (double)frx;
-        acc.fy += (double)fry;
+        sfx += frx;
+        sfy += fry;
         if (EVAL) {
             a.frep_out[i] = make_float2(frx, fry);
             a.fatt_out[i] = fa;
@@ -522,12 +540,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
             const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
             if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
             xout[i] = q;
-            acc.mn = fminf(acc.mn, fminf(q.x, q.y));
-            acc.mx = fmaxf(acc.mx, fmaxf(q.x, q.y));
+            mn = fminf(mn, fminf(q.x, q.y));
+            mx = fmaxf(mx, fmaxf(q.x, q.y));
         }
     }
     if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
-    block_publish(acc, st, cur ^ 1, !EVAL);
+    block_publish(mn, mx, sfx, sfy, st, cur ^ 1, !EVAL);
     if (!EVAL && advance && blockIdx.x == 0 && threadIdx.x == 0) st->iter = t + 1;
 }
 
@@ -551,12 +569,8 @@ cudaError_t launch_fft_sort(const NodeLaunch& a, int advance, cudaStream_t s) {
     const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
     if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
     const int nb = blocks_for(a.n, kNodeThreads);
-    switch (a.k) {
-        case 1: k_bin<1><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
-        case 2: k_bin<2><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
-        case 3: k_bin<3><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
-        default: return cudaErrorInvalidValue;
-    }
+    k_grid<<<1, 32, 0, s>>>(a, advance);
+    k_bin<<<nb, kNodeThreads, 0, s>>>(a);
     k_scan_partial<<<scan_blocks, kScanThreads, 0, s>>>(a);
     k_scan_top<<<1, kScanThreads, 0, s>>>(a, scan_blocks, advance);
     k_scan_add<<<blocks_for(a.nbox_max, kNodeThreads), kNodeThreads, 0, s>>>(a);
@@ -575,20 +589,20 @@ cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <int K>
-static void back_k(const NodeLaunch& a, int eval, cudaStream_t s) {
-    const int nb = blocks_for(a.n, kNodeThreads);
-    if (eval) k_gather_update<K, true><<<nb, kNodeThreads, 0, s>>>(a);
-    else k_gather_update<K, false><<<nb, kNodeThreads, 0, s>>>(a);
-}
-
 cudaError_t launch_fft_back(const NodeLaunch& a, int eval, cudaStream_t s) {
+    const int nb = blocks_for(a.n, kNodeThreads);
     switch (a.k) {
-        case 1: back_k<1>(a, eval, s); break;
-        case 2: back_k<2>(a, eval, s); break;
-        case 3: back_k<3>(a, eval, s); break;
+        case 1: k_gather_sorted<1><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
+        case 2: k_gather_sorted<2><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
+        case 3: k_gather_sorted<3><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
         default: return cudaErrorInvalidValue;
     }
+    // attraction + update read the repulsion from frep_out as a single "chunk"
+    NodeLaunch b = a;
+    b.part = a.frep_out;
+    b.nchunks = 1;
+    if (eval) k_edge_update<true><<<nb, kNodeThreads, 0, s>>>(b, 0);
+    else k_edge_update<false><<<nb, kNodeThreads, 0, s>>>(b, 0);
     return cudaGetLastError();
 }
 

@@ -89,6 +89,9 @@ struct tfdp_graph {
     float2* fatt_buf = nullptr;
     DevParams* dprm = nullptr;
     DevState* dst = nullptr;
+    double* step_table = nullptr;  // device, step_capacity entries
+    int step_capacity = 0;
+    std::vector<double> step_host;  // staging for the table upload
 
     // FFT arena
     void* fft_mem = nullptr;
@@ -222,6 +225,9 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     }
     free_execs(g);
     const int Gs = (int)align_up((size_t)G_max, 4);
+    // column stride of the transposed spectra: the row kernels write whole blocks of up
+    // to 32 rows (16 row pairs), so pad to 32
+    const int ystride = (int)align_up((size_t)G_max, 32);
     const size_t NH = (size_t)P / 2 + 1;
     const size_t n = (size_t)std::max<int64_t>(g->n, 1);
     Arena A;
@@ -232,8 +238,8 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     size_t o_sxy = A.take(sizeof(float2) * n);
     size_t o_perm = A.take(sizeof(int) * n);
     size_t o_gin = A.take(sizeof(float) * 3 * (size_t)Gs * Gs);
-    size_t o_T1 = A.take(sizeof(float2) * 3 * NH * Gs);
-    size_t o_T2 = A.take(sizeof(float2) * 3 * NH * Gs);
+    size_t o_T1 = A.take(sizeof(float2) * 3 * NH * ystride);
+    size_t o_T2 = A.take(sizeof(float2) * 3 * NH * ystride);
     size_t o_gout = A.take(sizeof(float4) * (size_t)Gs * Gs);
     size_t o_S1 = A.take(sizeof(float2) * 3 * NH * P);
     size_t o_sK = A.take(sizeof(float) * NH * P);
@@ -265,7 +271,7 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->logP = logP;
     g->G_max = G_max;
     g->Gs = Gs;
-    g->ystride = Gs;
+    g->ystride = ystride;
     g->nbox_max = nbox_max;
     g->fft_k = g->params.k_interp;
     g->fft_grid_max = g->params.grid_max;
@@ -285,7 +291,26 @@ tfdp_status alloc_fft(tfdp_graph* g) {
 }
 
 tfdp_status upload_params(tfdp_graph* g) {
+    // step schedule s_t = s0 (s_min / s0)^(t / (T - 1)), computed in FP64 on the host
+    const int T = g->params.total_iters;
+    if (T > g->step_capacity) {
+        CK(cudaStreamSynchronize(g->stream));
+        if (g->step_table) CK(cudaFree(g->step_table));
+        g->step_table = nullptr;
+        g->step_capacity = 0;
+        CK(cudaMalloc(&g->step_table, sizeof(double) * (size_t)T));
+        g->step_capacity = T;
+    }
+    CK(cudaStreamSynchronize(g->stream));  // the staging vector is reused below
+    g->step_host.resize((size_t)T);
+    for (int t = 0; t < T; ++t)
+        g->step_host[(size_t)t] = (T <= 1) ? g->params.step0
+                                           : g->params.step0 * std::pow(g->params.step_min / g->params.step0,
+                                                                        (double)t / (double)(T - 1));
+    CK(cudaMemcpyAsync(g->step_table, g->step_host.data(), sizeof(double) * (size_t)T, cudaMemcpyHostToDevice,
+                       g->stream));
     g->dp = make_dev_params(g->params, g->P ? g->P : 128, g->logP ? g->logP : 7);
+    g->dp.step_table = g->step_table;
     CK(cudaMemcpyAsync(g->dprm, &g->dp, sizeof(DevParams), cudaMemcpyHostToDevice, g->stream));
     // dp lives in the graph object, which outlives the copy; the copy is ordered
     // before any later kernel on the stream.
@@ -342,7 +367,8 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
 
 // Kernels launched per iteration (count of the launches above).
 int kernels_per_iteration(const tfdp_graph* g) {
-    return g->params.rep_mode == TFDP_REP_EXACT ? 2 : (5 + 1 + 2 + 1 + 1 + 1 + 1);
+    // FFT: grid + bin + 3 scan + scatter, spread, 2 spectrum, rows, cols, rows, gather + edge
+    return g->params.rep_mode == TFDP_REP_EXACT ? 2 : (6 + 1 + 2 + 1 + 1 + 1 + 2);
 }
 
 long long exec_key_of(const tfdp_graph* g) {
@@ -712,6 +738,7 @@ tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
         if (g->ev[i]) cudaEventDestroy(g->ev[i]);
     if (g->fft_mem) cudaFree(g->fft_mem);
     if (g->node_mem) cudaFree(g->node_mem);
+    if (g->step_table) cudaFree(g->step_table);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
     return TFDP_OK;

@@ -114,6 +114,25 @@ def test_fft_forces_small(tfdp, k, policy):
     assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
 
 
+@pytest.mark.parametrize("grid_max,k", [(40, 3), (100, 2), (255, 1), (511, 3), (1023, 2),
+                                         (2047, 3), (4095, 3)])
+def test_fft_forces_every_fft_size(tfdp, grid_max, k):
+    """FFT sizes P = 128 .. 8192; the oracle uses its own smallest P >= 2G - 1, so this
+    also checks that the result does not depend on the circulant size."""
+    rng = np.random.default_rng(grid_max + k)
+    n = 4099
+    half = min(0.5 * grid_max / k, 120.0)
+    e = synth.erdos_renyi(n, 2 * n, rng)
+    xy = rng.uniform(-half, half, size=(n, 2)).astype(np.float32)
+    with tfdp.Graph(n, e, xy, _params(tfdp, k_interp=k, grid_max=grid_max)) as g:
+        fr, _ = g.eval_forces()
+        st = g.stats()
+    grid = oracle.grid_policy(xy, k, 50, grid_max, 1)
+    assert st["grid_G"] == grid["G"]
+    ref = oracle.rep_fft(xy.astype(np.float64), 2.0, k, grid=grid, xy_f32=xy)
+    assert record("fft_P%d_k%d" % (st["fft_P"], k), rel_l2(fr, ref)) <= FORCE_TOL
+
+
 def test_fft_forces_sbm_100k(tfdp):
     """Config 2: SBM n=100k, 20 blocks, mean degree 10, k=3, grid up to 256^2."""
     e, xy = synth.sbm_100k()
