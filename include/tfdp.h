@@ -112,10 +112,11 @@ enum {
     TFDP_STAGE_ROWS_FWD = 3,      /* FFT path: forward transform along x */
     TFDP_STAGE_COLS = 4,          /* FFT path: transform along y, spectral product, inverse */
     TFDP_STAGE_ROWS_INV = 5,      /* FFT path: inverse transform along x */
-    TFDP_STAGE_GATHER_UPDATE = 6, /* FFT path: back-projection, then attraction + update (2 kernels) */
+    TFDP_STAGE_GATHER_UPDATE = 6, /* FFT path: back-projection + update */
     TFDP_STAGE_EXACT = 7,         /* exact path: all-pairs repulsion */
     TFDP_STAGE_EDGE_UPDATE = 8,   /* exact path: attraction + update */
-    TFDP_NUM_STAGES = 9
+    TFDP_STAGE_ATTRACT = 9,       /* FFT path: attraction, on a second stream concurrent with stages 0-5 */
+    TFDP_NUM_STAGES = 10
 };
 
 typedef struct tfdp_graph tfdp_graph;

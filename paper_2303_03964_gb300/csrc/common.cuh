@@ -71,6 +71,7 @@ struct DevState {
     double net_frep[2];       // FP64 sum of frep over nodes (last iteration)
     unsigned int done_blocks; // completion counter of the last kernel of an iteration
     int pad_;
+    unsigned long long scan_ticket;  // tickets of the single-pass scan (launch * tiles + tile)
 };
 
 // ---------------------------------------------------------------- ordered floats

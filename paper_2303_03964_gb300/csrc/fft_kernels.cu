@@ -283,17 +283,15 @@ struct RegGeom {
     static constexpr size_t cols_smem = (size_t)CG * 3 * P * sizeof(float2);
 };
 
+// Forward row transforms of row block `blk` (2 RG rows x 3 channels) of a source into
+// out[c][kx][ystride] (half spectrum along x, column-major).
 template <int LOGP, class Src>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
-    k_rows_fwd_r(Src src, float2* __restrict__ T1, int ystride, const float2* __restrict__ tw,
-                 const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
+__device__ __forceinline__ void rows_fwd_body(const Src& src, int nrows, int blk, float2* __restrict__ out,
+                                              int ystride, const float2* __restrict__ tw, float2* sm) {
     using Gm = RegGeom<LOGP>;
     constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
-    extern __shared__ float2 sm[];
-    if (!src.active(st)) return;
-    src.bind(st, prm);
-    const int G = src.rows(st);
-    const int ybase = blockIdx.x * (2 * RG);
+    const int G = nrows;
+    const int ybase = blk * (2 * RG);
     if (ybase >= G) return;
     const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
     const int y0 = ybase + 2 * lr;
@@ -313,13 +311,13 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
         for (int r = 0; r < 8; ++r) smr[c * P + swz(8 * t + r)] = v[c][r];
     __syncthreads();
     // split Z = FFT(a + i b) into FFT(a), FFT(b); one thread per (channel, kx) writes
-    // 2 RG consecutive rows (RG row pairs) of T1[c][kx][.]
+    // 2 RG consecutive rows (RG row pairs) of out[c][kx][.]
     for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
         const int c = idx / NH;
         const int kx = idx - c * NH;
         const int pk = swz(pos_of_freq<LOGP>(kx));
         const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
-        float4* dst = reinterpret_cast<float4*>(T1 + ((size_t)c * NH + kx) * ystride + ybase);
+        float4* dst = reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + ybase);
 #pragma unroll
         for (int q = 0; q < RG; ++q) {
             const float2* seq = sm + ((size_t)q * 3 + c) * P;
@@ -329,11 +327,29 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
     }
 }
 
+// Blocks [0, data_blocks): rows of the spread grid into T1. Blocks after that: rows of
+// the sampled kernels into S1, only in an iteration that rebuilds the spectrum.
 template <int LOGP>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG)
-    k_cols_r(const float2* __restrict__ T1, float2* __restrict__ T2, int ystride, const float* __restrict__ specK,
-             const float* __restrict__ specHx, const float* __restrict__ specHy, const float2* __restrict__ tw,
-             const DevState* __restrict__ st) {
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 3 : 1)
+    k_rows_fwd_r(GridSource gsrc, int data_blocks, float2* __restrict__ T1, int ystride, float2* __restrict__ S1,
+                 const float2* __restrict__ tw, const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
+    extern __shared__ float2 sm[];
+    if ((int)blockIdx.x < data_blocks) {
+        rows_fwd_body<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
+    } else {
+        if (st->spec_dirty == 0) return;
+        KernelSource ks;
+        ks.P = 1 << LOGP;
+        ks.bind(st, prm);
+        rows_fwd_body<LOGP>(ks, ks.P, blockIdx.x - data_blocks, S1, 1 << LOGP, tw, sm);
+    }
+}
+
+template <int LOGP>
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<LOGP>::T * RegGeom<LOGP>::CG <= 256 ? 3 : 1)
+    k_cols_r(const float2* __restrict__ T1, float2* __restrict__ T2, int ystride, float* __restrict__ specK,
+             float* __restrict__ specHx, float* __restrict__ specHy, const float2* __restrict__ S1,
+             const float2* __restrict__ tw, const DevState* __restrict__ st) {
     using Gm = RegGeom<LOGP>;
     constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
     extern __shared__ float2 sm[];
@@ -343,6 +359,37 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG)
     const int G = st->grid.G;
     float2* smc = sm + (size_t)lc * 3 * P;
     float2 v[3][8];
+    // kernel spectra at this thread's output positions 8t .. 8t+7 (digit-reversed order)
+    float K[8], hx[8], hy[8];
+    const size_t so = (size_t)(valid ? kx : 0) * P + 8 * t;
+    if (st->spec_dirty) {
+        // rebuild: forward transform along y of the row-transformed kernel samples
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                v[c][r] = valid ? S1[((size_t)c * NH + kx) * P + t + r * T] : make_float2(0.f, 0.f);
+        reg_fft_forward<LOGP, 3>(v, smc, tw, t);
+        const float inv = 1.0f / ((float)P * (float)P);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            K[r] = v[0][r].x * inv;
+            hx[r] = v[1][r].y * inv;
+            hy[r] = v[2][r].y * inv;
+        }
+        if (valid) {
+            float4* pK = reinterpret_cast<float4*>(specK + so);
+            float4* pX = reinterpret_cast<float4*>(specHx + so);
+            float4* pY = reinterpret_cast<float4*>(specHy + so);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                pK[h] = make_float4(K[4 * h], K[4 * h + 1], K[4 * h + 2], K[4 * h + 3]);
+                pX[h] = make_float4(hx[4 * h], hx[4 * h + 1], hx[4 * h + 2], hx[4 * h + 3]);
+                pY[h] = make_float4(hy[4 * h], hy[4 * h + 1], hy[4 * h + 2], hy[4 * h + 3]);
+            }
+        }
+        __syncthreads();  // shared memory is reused by the data transform
+    }
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -352,14 +399,15 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG)
         }
     reg_fft_forward<LOGP, 3>(v, smc, tw, t);
     if (valid) {
-        const size_t so = (size_t)kx * P + 8 * t;
+        // spectra at the output positions; loaded here (not before the transform) to keep
+        // them out of the registers the transform needs; after a rebuild this re-reads
+        // what this thread just wrote
         const float4* pK = reinterpret_cast<const float4*>(specK + so);
         const float4* pX = reinterpret_cast<const float4*>(specHx + so);
         const float4* pY = reinterpret_cast<const float4*>(specHy + so);
-        float K[8], hx[8], hy[8];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float4 a = __ldg(pK + h), b = __ldg(pX + h), d = __ldg(pY + h);
+            const float4 a = pK[h], b = pX[h], d = pY[h];
             K[4 * h] = a.x; K[4 * h + 1] = a.y; K[4 * h + 2] = a.z; K[4 * h + 3] = a.w;
             hx[4 * h] = b.x; hx[4 * h + 1] = b.y; hx[4 * h + 2] = b.z; hx[4 * h + 3] = b.w;
             hy[4 * h] = d.x; hy[4 * h + 1] = d.y; hy[4 * h + 2] = d.z; hy[4 * h + 3] = d.w;
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG)
 }
 
 template <int LOGP>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG)
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 4 : 1)
     k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
                  const float2* __restrict__ tw, const DevState* __restrict__ st) {
     using Gm = RegGeom<LOGP>;
@@ -456,7 +504,7 @@ static cudaError_t set_attrs() {
     if (LOGP <= kMaxRegLogP) {
         using Rg = RegGeom<(LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP)>;
         constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
-        if ((e = cudaFuncSetAttribute(k_rows_fwd_r<L, GridSource>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_rows_fwd_r<L>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_cols_r<L>, A, (int)Rg::cols_smem)) != cudaSuccess) return e;
         if ((e = cudaFuncSetAttribute(k_rows_inv_r<L>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
     }
@@ -486,6 +534,8 @@ template <int LOGP>
 static cudaError_t launch_spectrum_impl(const FftLaunch& a, cudaStream_t s) {
     using Gm = FftGeom<LOGP>;
     constexpr int P = Gm::P;
+    // the register-resident kernels rebuild the spectrum inside the row and column passes
+    if (LOGP <= kMaxRegLogP) return cudaSuccess;
     cudaError_t e = ensure_attrs<LOGP>();
     if (e != cudaSuccess) return e;
     KernelSource ks;
@@ -511,7 +561,9 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
         constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
         using Rg = RegGeom<L>;
         const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-        k_rows_fwd_r<L, GridSource><<<blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(gs, a.T1, a.ystride, a.tw, a.st, a.prm);
+        const int spec_blocks = Rg::P / (2 * Rg::RG);
+        k_rows_fwd_r<L><<<blocks + spec_blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(gs, blocks, a.T1, a.ystride, a.S1,
+                                                                                  a.tw, a.st, a.prm);
         return cudaGetLastError();
     }
     const int row_blocks = (a.G_max + Gm::RPC - 1) / Gm::RPC;
@@ -529,7 +581,8 @@ static cudaError_t launch_cols_impl(const FftLaunch& a, cudaStream_t s) {
         constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
         using Rg = RegGeom<L>;
         const int blocks = (P / 2 + 1 + Rg::CG - 1) / Rg::CG;
-        k_cols_r<L><<<blocks, Rg::T * Rg::CG, Rg::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy, a.tw, a.st);
+        k_cols_r<L><<<blocks, Rg::T * Rg::CG, Rg::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy,
+                                                                   a.S1, a.tw, a.st);
         return cudaGetLastError();
     }
     k_cols<LOGP><<<P / 2 + 1, 256, Gm::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy, a.tw, a.st);

@@ -51,9 +51,15 @@ struct NodeLaunch {
     int* cnt;              // nbox_max (zero between iterations)
     int* off;              // nbox_max + 1
     int* bsum;             // scan block sums
-    int2* keyslot;         // n
-    float2* sxy;           // n, cell-sorted positions
-    int* perm;             // n, node id of each sorted slot
+    unsigned long long* scan_status;  // one status word per scan tile
+    int2* keyslot;         // n, (box, slot in box) per visit slot
+    // Visit orders: iteration t visits nodes in order vperm[t & 1] (the cell-sorted order
+    // of iteration t - 1) with positions vxy[t & 1]; its sort writes the new order into
+    // vperm[t & 1 ^ 1] / vxy[t & 1 ^ 1] (old positions, which the update then overwrites
+    // with the new ones), and rank[i] = slot of node i in the new order.
+    int* vperm[2];         // n each
+    float2* vxy[2];        // n each
+    int* rank;             // n
     float* gin;            // spread output
     int Gs;
     const float4* gout;    // grid output
@@ -67,13 +73,18 @@ struct NodeLaunch {
 
 // Positions -> bbox slot `slot` of the state (min / max over both coordinates).
 cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s);
-// FFT path, before the grid interaction: bin + scan + scatter (5 kernels), spread (1).
-// advance != 0: this is an iteration (t_cur = iter, iter += 1 at the scan).
-cudaError_t launch_fft_sort(const NodeLaunch& a, int advance, cudaStream_t s);
+// Visit order `slot` := caller order (identity permutation, positions xy[slot]).
+cudaError_t launch_order_reset(const NodeLaunch& a, int slot, cudaStream_t s);
+// FFT path, first kernel of an iteration: grid policy, t_cur = iter, step, spectrum key.
+cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s);
+// FFT path, before the grid interaction: bin + scan + scatter (3 kernels), spread (1).
+cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s);
 cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s);
-// FFT path, after the grid interaction: gather + attraction + update (eval = 0) or
-// gather + attraction written to frep_out / fatt_out (eval = 1). 1 kernel.
-cudaError_t launch_fft_back(const NodeLaunch& a, int eval, cudaStream_t s);
+// FFT path: attraction into fatt_out (caller order; independent of the grid, 1 kernel).
+cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s);
+// FFT path, after the grid interaction and launch_attract: gather + update (eval = 0;
+// advance != 0 moves the iteration counter on) or gather into frep_out (eval = 1).
+cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStream_t s);
 // Exact path: all-pairs repulsion (1 kernel), then attraction + update (eval = 0)
 // or outputs (eval = 1) (1 kernel).
 cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s);

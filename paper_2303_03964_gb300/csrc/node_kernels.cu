@@ -8,10 +8,10 @@
 //   k_scatter        cell-sorted copy of the positions
 //   k_spread         Lagrange projection onto the k x k nodes of each box (Sec. 3.4,
 //                    step 1): rho, m^x, m^y; one thread owns one box, so no atomics
-//   k_gather_sorted  back-projection (step 3) in cell-sorted order
+//   k_attract        attraction over the CSR (Eq. newforce), caller order, on a side stream
+//   k_gather_update  back-projection (step 3) + capped step (update), cell-sorted order
 //   k_exact          tiled all-pairs repulsion (Eq. repfK), FP32
-//   k_edge_update    attraction over the CSR (Eq. newforce) + capped step (update),
-//                    on the repulsion of either path
+//   k_edge_update    attraction + capped step for the exact path
 //
 // Node coordinates relative to their box origin are formed exactly (TwoSum and an
 // FMA-exact product), so that FP32 coordinates of magnitude |x| ~ 10^3 keep the
@@ -215,29 +215,65 @@ __global__ void k_grid(NodeLaunch a, int advance) {
     }
 }
 
-// Box of every node (the FP32 decision) and its slot in the box (counting-sort histogram).
+// Box of every node (the FP32 decision) and its slot in the box (counting-sort
+// histogram), visiting nodes in the previous iteration's cell-sorted order: neighbouring
+// lanes mostly share a box, so one atomic serves all lanes of a warp with that box.
 __global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a) {
     const DevState* st = a.st;
     const int cur = (int)(st->t_cur & 1);
-    const float2* __restrict__ xy = a.xy[cur];
+    const float2* __restrict__ vxy = a.vxy[cur];
     const float lo = st->grid.lo_f, h = st->grid.h_f;
     const int n_int = st->grid.n_int;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const float2 p = xy[i];
+    const int lane = threadIdx.x & 31;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        const float2 p = vxy[v];
         float tq;
         const int bx = box_of(p.x, lo, h, n_int, &tq);
         const int by = box_of(p.y, lo, h, n_int, &tq);
         const int key = by * n_int + bx;
-        const int slot = atomicAdd(a.cnt + key, 1);
-        a.keyslot[i] = make_int2(key, slot);
+        const unsigned active = __activemask();
+        const unsigned same = __match_any_sync(active, key);
+        const int leader = __ffs(same) - 1;
+        int base = 0;
+        if (lane == leader) base = atomicAdd(a.cnt + key, __popc(same));
+        base = __shfl_sync(same, base, leader);
+        a.keyslot[v] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
+    }
+}
+
+// Visit order `slot` := identity (node v at slot v) with the caller-order positions.
+__global__ void __launch_bounds__(kNodeThreads) k_order_reset(NodeLaunch a, int slot) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        a.vperm[slot][v] = v;
+        a.vxy[slot][v] = a.xy[slot][v];
     }
 }
 
 // ---------------------------------------------------------------- FFT path: scan
-__global__ void __launch_bounds__(kScanThreads) k_scan_partial(NodeLaunch a) {
-    const int n_int = a.st->grid.n_int;
+// Single-pass exclusive scan of the box counts with decoupled look-back. Each CTA takes
+// a ticket; ticket order is launch order, so a CTA only waits for CTAs that are already
+// running. Tile status words (flag | epoch | value) carry the launch epoch, so stale
+// words of earlier launches read as "not ready" and nothing needs clearing. Waits are
+// bounded: on timeout the CTA sets FLAG_WAIT_TIMEOUT and carries on with what it has
+// (offsets then fail the scatter's range check instead of faulting).
+constexpr unsigned long long kStAggregate = 1ULL << 62;
+constexpr unsigned long long kStPrefix = 2ULL << 62;
+constexpr int kLookbackSpinLimit = 1 << 20;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, int ntiles,
+                                                                 unsigned long long* __restrict__ status) {
+    __shared__ unsigned long long s_ticket;
+    __shared__ int s_w[32];
+    __shared__ int s_prefix;
+    DevState* st = a.st;
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&st->scan_ticket, 1ULL);
+    __syncthreads();
+    const unsigned long long tk = s_ticket;
+    const int tile = (int)(tk % (unsigned long long)ntiles);
+    const unsigned long long epoch = (tk / (unsigned long long)ntiles) & 0x3FFFFFFFULL;
+    const int n_int = st->grid.n_int;
     const int nbox = n_int * n_int;
-    const int i0 = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;
+    const int i0 = tile * kScanChunk + threadIdx.x * kScanItems;
     int v[kScanItems];
     const int4* src = reinterpret_cast<const int4*>(a.cnt + i0);
     const int4 c0 = src[0], c1 = src[1];
@@ -256,7 +292,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partial(NodeLaunch a) {
         const int y = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += y;
     }
-    __shared__ int s_w[32];
     if (lane == 31) s_w[w] = incl;
     __syncthreads();
     if (w == 0) {
@@ -267,70 +302,93 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_partial(NodeLaunch a) {
             const int y = __shfl_up_sync(0xffffffffu, xi, o);
             if (lane >= o) xi += y;
         }
-        s_w[lane] = xi - x;
+        s_w[lane] = xi - x;  // exclusive prefix of warp totals
+        const int total = __shfl_sync(0xffffffffu, xi, 31);
+        const unsigned long long tag = epoch << 32;
+        volatile unsigned long long* vs = status;
+        int prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) vs[0] = kStPrefix | tag | (unsigned)total;
+        } else {
+            if (lane == 0) {
+                vs[tile] = kStAggregate | tag | (unsigned)total;
+                __threadfence();
+            }
+            __syncwarp();
+            // warp-parallel look-back: lane l inspects tile (end - 1 - l) of a window of 32
+            int end = tile;
+            int spins = 0;
+            bool done = false;
+            while (!done) {
+                const int p = end - 1 - lane;
+                unsigned long long sw = 0;
+                bool ready = true;
+                if (p >= 0) {
+                    sw = vs[p];
+                    ready = ((sw >> 32) & 0x3FFFFFFFULL) == epoch && (sw >> 62) != 0;
+                }
+                if (__all_sync(0xffffffffu, ready) == 0) {
+                    if (++spins > kLookbackSpinLimit) {
+                        if (lane == 0) atomicOr(&st->flags, FLAG_WAIT_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                // nearest lane holding an inclusive prefix; sum the values up to it
+                const bool is_prefix = (p >= 0) && ((sw >> 62) == (kStPrefix >> 62));
+                const unsigned pm = __ballot_sync(0xffffffffu, is_prefix);
+                const int first = pm ? (__ffs(pm) - 1) : 31;
+                int val = (p >= 0 && lane <= first) ? (int)(unsigned)(sw & 0xFFFFFFFFULL) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+                prefix += val;
+                if (pm || end - 32 <= 0) done = true;
+                end -= 32;
+            }
+            if (lane == 0) {
+                __threadfence();
+                vs[tile] = kStPrefix | tag | (unsigned)(prefix + total);
+            }
+        }
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
-    int run = s_w[w] + incl - tsum;
+    int run = s_prefix + s_w[w] + incl - tsum;
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
-        if (i0 + q < nbox) a.off[i0 + q] = run;
+        if (i0 + q < nbox) {
+            a.off[i0 + q] = run;
+            a.cnt[i0 + q] = 0;  // ready for the next histogram
+        }
         run += v[q];
     }
-    if (threadIdx.x == kScanThreads - 1) a.bsum[blockIdx.x] = run;
-}
-
-// Exclusive scan of the block sums (at most kScanThreads of them), one CTA.
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(NodeLaunch a, int nblocks, int advance) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = threadIdx.x < nblocks ? a.bsum[threadIdx.x] : 0;
-    int incl = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    __shared__ int s_w[32];
-    if (lane == 31) s_w[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        const int v = s_w[lane];
-        int vi = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, vi, o);
-            if (lane >= o) vi += y;
-        }
-        s_w[lane] = vi - v;
-    }
-    __syncthreads();
-    if (threadIdx.x < nblocks) a.bsum[threadIdx.x] = s_w[w] + incl - x;
-    if (threadIdx.x == 0 && advance) a.st->iter = a.st->t_cur + 1;
-}
-
-__global__ void __launch_bounds__(kNodeThreads) k_scan_add(NodeLaunch a) {
-    const int n_int = a.st->grid.n_int;
-    const int nbox = n_int * n_int;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < nbox) {
-        a.off[i] += a.bsum[i / kScanChunk];
-        a.cnt[i] = 0;
-    }
-    if (i == 0) a.off[nbox] = a.n;
+    // off[nbox] = n, written by the thread whose items end at or contain nbox
+    if (i0 <= nbox && (nbox < i0 + kScanItems || (nbox == i0 + kScanItems && i0 + kScanItems == ntiles * kScanChunk)))
+        a.off[nbox] = a.n;
 }
 
 // ---------------------------------------------------------------- FFT path: scatter
 __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
     const int cur = (int)(a.st->t_cur & 1);
-    const float2* __restrict__ xy = a.xy[cur];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        const int2 ks = a.keyslot[i];
+    const int* __restrict__ vperm = a.vperm[cur];
+    const float2* __restrict__ vxy = a.vxy[cur];
+    int* __restrict__ nperm = a.vperm[cur ^ 1];
+    float2* __restrict__ nxy = a.vxy[cur ^ 1];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        const int2 ks = a.keyslot[v];
         const int pos = a.off[ks.x] + ks.y;
         if ((unsigned)pos >= (unsigned)a.n) {
             atomicOr(&a.st->flags, FLAG_SORT_RANGE);
             continue;
         }
-        a.sxy[pos] = xy[i];
-        a.perm[pos] = i;
+        const int i = vperm[v];
+        if ((unsigned)i >= (unsigned)a.n) {
+            atomicOr(&a.st->flags, FLAG_SORT_RANGE);
+            continue;
+        }
+        nxy[pos] = vxy[v];
+        nperm[pos] = i;
+        a.rank[i] = pos;
     }
 }
 
@@ -343,6 +401,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
     const int nbox = g.n_int * g.n_int;
     const AxisGeom ag = axis_geom(g);
     const size_t plane = (size_t)a.Gs * a.Gs;
+    const float2* __restrict__ sxy = a.vxy[(int)(a.st->t_cur & 1) ^ 1];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
         const int by = b / g.n_int;
         const int bx = b - by * g.n_int;
@@ -354,7 +413,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
         const int s0 = max(a.off[b], 0);
         const int s1 = min(a.off[b + 1], a.n);
         for (int s = s0; s < s1; ++s) {
-            const float2 p = a.sxy[s];
+            const float2 p = sxy[s];
             float ox, oy;
             box_offset(p.x, ag, &ox);
             box_offset(p.y, ag, &oy);
@@ -388,18 +447,50 @@ __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
     }
 }
 
-// ---------------------------------------------------------------- FFT path: gather
-// frep(i) = sum_p w_ip [ (x_i - y_p) A_p + O_p ]  (well-conditioned Eq. Fr1/Fr2).
-// Nodes are visited in cell-sorted order, so neighbouring threads read the same grid
-// values; the result goes to the node's caller-order slot. Attraction and the update
-// follow in k_edge_update (caller order), which reads these values.
-template <int K>
-__global__ void __launch_bounds__(kNodeThreads) k_gather_sorted(NodeLaunch a, float2* __restrict__ frep) {
-    const GridDesc g = a.st->grid;
+// ---------------------------------------------------------------- FFT path: attraction
+// fatt(i) in caller order (coalesced CSR rows); independent of the grid, so it runs
+// on a second stream while the sort, spread and FFT run.
+__global__ void __launch_bounds__(kNodeThreads) k_attract(NodeLaunch a) {
+    const int cur = (int)(a.st->t_cur & 1);  // set by k_grid, which precedes the fork
+    const float2* __restrict__ xin = a.xy[cur];
+    const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+        const int ii[2] = {base, base + (int)blockDim.x};
+        float2 pp[2], fa[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) pp[u] = xin[ii[u] < a.n ? ii[u] : base];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) fa[u] = attraction(ii[u] < a.n ? ii[u] : base, pp[u], a.rowptr, a.col, xin, alpha, beta);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (ii[u] < a.n) a.fatt_out[ii[u]] = fa[u];
+    }
+}
+
+// ---------------------------------------------------------------- FFT path: gather + update
+// frep(i) = sum_p w_ip [ (x_i - y_p) A_p + O_p ]  (well-conditioned Eq. Fr1/Fr2), then the
+// capped step with fatt(i). Nodes are visited in cell-sorted order, so neighbouring
+// threads read the same grid values and the next iteration's visit-order positions are
+// written contiguously; caller-order outputs are scattered through perm.
+template <int K, bool EVAL>
+__global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a, int advance) {
+    DevState* st = a.st;
+    const GridDesc g = st->grid;
     const AxisGeom ag = axis_geom(g);
+    const int cur = (int)(st->t_cur & 1);
+    const int nxt = cur ^ 1;
+    float2* __restrict__ sxy = a.vxy[nxt];  // old positions in the new order, then new ones
+    const int* __restrict__ perm = a.vperm[nxt];
+    float2* __restrict__ xout = a.xy[nxt];
+    const float step = (float)st->step_cur;
+    float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
+    unsigned bad = 0;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
-        const float2 p = a.sxy[s];
-        const int i = a.perm[s];
+        const float2 p = sxy[s];
+        const int i = perm[s];
+        if ((unsigned)i >= (unsigned)a.n) continue;  // only after a failed sort (flagged there)
+        const float2 fa = a.fatt_out[i];
         float ox, oy;
         const int bx = box_offset(p.x, ag, &ox);
         const int by = box_offset(p.y, ag, &oy);
@@ -423,8 +514,23 @@ __global__ void __launch_bounds__(kNodeThreads) k_gather_sorted(NodeLaunch a, fl
                 fry = fmaf(w, fmaf(dy[ly], v.x, v.z), fry);
             }
         }
-        frep[i] = make_float2(frx, fry);
+        sfx += frx;
+        sfy += fry;
+        if (EVAL) {
+            a.frep_out[i] = make_float2(frx, fry);
+        } else {
+            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
+            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+            xout[i] = q;
+            sxy[s] = q;  // next iteration's visit order is this iteration's sorted order
+            mn = fminf(mn, fminf(q.x, q.y));
+            mx = fmaxf(mx, fmaxf(q.x, q.y));
+        }
     }
+    if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+    block_publish(mn, mx, sfx, sfy, st, nxt, !EVAL);
+    // the last kernel of an iteration advances the counter (the side stream has joined)
+    if (!EVAL && advance && blockIdx.x == 0 && threadIdx.x == 0) st->iter = st->t_cur + 1;
 }
 
 // ---------------------------------------------------------------- exact path
@@ -511,6 +617,9 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
     if (i < a.n) a.part[(size_t)blockIdx.y * a.n + i] = make_float2(fx, fy);
 }
 
+// Attraction + update in caller order, on the repulsion summed over `nchunks` partial
+// arrays. Each thread takes two nodes per round so that their dependent loads
+// (row pointers, neighbour ids, neighbour positions) overlap.
 template <bool EVAL>
 __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int advance) {
     DevState* st = a.st;
@@ -522,26 +631,43 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
     const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
     float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
     unsigned bad = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        float frx = 0.0f, fry = 0.0f;
-        for (int c = 0; c < a.nchunks; ++c) {
-            const float2 v = a.part[(size_t)c * a.n + i];
-            frx += v.x;
-            fry += v.y;
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+        const int ii[2] = {base, base + (int)blockDim.x};
+        float2 fr[2], pp[2], fa[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ii[u] < a.n ? ii[u] : base;
+            fr[u] = make_float2(0.0f, 0.0f);
+            for (int c = 0; c < a.nchunks; ++c) {
+                const float2 v = a.part[(size_t)c * a.n + i];
+                fr[u].x += v.x;
+                fr[u].y += v.y;
+            }
+            pp[u] = xin[i];
         }
-        const float2 p = xin[i];
-        const float2 fa = attraction(i, p, a.rowptr, a.col, xin, alpha, beta);
-        sfx += frx;
-        sfy += fry;
-        if (EVAL) {
-            a.frep_out[i] = make_float2(frx, fry);
-            a.fatt_out[i] = fa;
-        } else {
-            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
-            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
-            xout[i] = q;
-            mn = fminf(mn, fminf(q.x, q.y));
-            mx = fmaxf(mx, fmaxf(q.x, q.y));
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ii[u] < a.n ? ii[u] : base;
+            fa[u] = attraction(i, pp[u], a.rowptr, a.col, xin, alpha, beta);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int i = ii[u];
+            if (i >= a.n) continue;
+            sfx += fr[u].x;
+            sfy += fr[u].y;
+            if (EVAL) {
+                a.frep_out[i] = fr[u];
+                a.fatt_out[i] = fa[u];
+            } else {
+                const float2 q = capped_step(pp[u], make_float2(fr[u].x + fa[u].x, fr[u].y + fa[u].y), step);
+                if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+                xout[i] = q;
+
+                mn = fminf(mn, fminf(q.x, q.y));
+                mx = fmaxf(mx, fmaxf(q.x, q.y));
+            }
         }
     }
     if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
@@ -557,6 +683,12 @@ static inline int blocks_for(long long work, int threads) {
     return (int)b;
 }
 
+cudaError_t launch_order_reset(const NodeLaunch& a, int slot, cudaStream_t s) {
+    if (a.n == 0 || !a.rank) return cudaSuccess;
+    k_order_reset<<<blocks_for(a.n, kNodeThreads), kNodeThreads, 0, s>>>(a, slot);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
     int blocks = blocks_for(a.n, kNodeThreads);
@@ -565,15 +697,17 @@ cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_sort(const NodeLaunch& a, int advance, cudaStream_t s) {
+cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s) {
+    k_grid<<<1, 32, 0, s>>>(a, advance);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
     if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
     const int nb = blocks_for(a.n, kNodeThreads);
-    k_grid<<<1, 32, 0, s>>>(a, advance);
     k_bin<<<nb, kNodeThreads, 0, s>>>(a);
-    k_scan_partial<<<scan_blocks, kScanThreads, 0, s>>>(a);
-    k_scan_top<<<1, kScanThreads, 0, s>>>(a, scan_blocks, advance);
-    k_scan_add<<<blocks_for(a.nbox_max, kNodeThreads), kNodeThreads, 0, s>>>(a);
+    k_scan_lookback<<<scan_blocks, kScanThreads, 0, s>>>(a, scan_blocks, a.scan_status);
     k_scatter<<<nb, kNodeThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -589,20 +723,20 @@ cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_back(const NodeLaunch& a, int eval, cudaStream_t s) {
+cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s) {
+    if (a.n == 0) return cudaSuccess;
+    k_attract<<<blocks_for(a.n, 2 * kNodeThreads), kNodeThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
     const int nb = blocks_for(a.n, kNodeThreads);
     switch (a.k) {
-        case 1: k_gather_sorted<1><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
-        case 2: k_gather_sorted<2><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
-        case 3: k_gather_sorted<3><<<nb, kNodeThreads, 0, s>>>(a, a.frep_out); break;
+        case 1: eval ? k_gather_update<1, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<1, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        case 2: eval ? k_gather_update<2, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<2, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        case 3: eval ? k_gather_update<3, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<3, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
         default: return cudaErrorInvalidValue;
     }
-    // attraction + update read the repulsion from frep_out as a single "chunk"
-    NodeLaunch b = a;
-    b.part = a.frep_out;
-    b.nchunks = 1;
-    if (eval) k_edge_update<true><<<nb, kNodeThreads, 0, s>>>(b, 0);
-    else k_edge_update<false><<<nb, kNodeThreads, 0, s>>>(b, 0);
     return cudaGetLastError();
 }
 
@@ -618,7 +752,7 @@ cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s)
 }
 
 cudaError_t launch_edge_update(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
-    const int nb = blocks_for(a.n, kNodeThreads);
+    const int nb = blocks_for(a.n, 2 * kNodeThreads);
     if (eval) k_edge_update<true><<<nb, kNodeThreads, 0, s>>>(a, advance);
     else k_edge_update<false><<<nb, kNodeThreads, 0, s>>>(a, advance);
     return cudaGetLastError();

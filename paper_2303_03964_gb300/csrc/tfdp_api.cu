@@ -101,8 +101,10 @@ struct tfdp_graph {
     int* off = nullptr;
     int* bsum = nullptr;
     int2* keyslot = nullptr;
-    float2* sxy = nullptr;
-    int* perm = nullptr;
+    int* vperm[2] = {nullptr, nullptr};
+    float2* vxy[2] = {nullptr, nullptr};
+    int* rank = nullptr;
+    bool last_was_eval = false;  // which visit-order buffer holds the latest sort
     float* gin = nullptr;
     float2* T1 = nullptr;
     float2* T2 = nullptr;
@@ -120,6 +122,11 @@ struct tfdp_graph {
     // stage timing (events around the stages of an iteration)
     bool timing = false;
     cudaEvent_t ev[TFDP_NUM_STAGES + 1] = {};
+    cudaEvent_t ev_attract[2] = {};
+
+    // side stream for the attraction of the FFT path (fork / join events)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
     NodeLaunch node_launch() const {
         NodeLaunch a{};
@@ -136,9 +143,13 @@ struct tfdp_graph {
         a.cnt = cnt;
         a.off = off;
         a.bsum = bsum;
+        a.scan_status = (unsigned long long*)bsum;
         a.keyslot = keyslot;
-        a.sxy = sxy;
-        a.perm = perm;
+        a.vperm[0] = vperm[0];
+        a.vperm[1] = vperm[1];
+        a.vxy[0] = vxy[0];
+        a.vxy[1] = vxy[1];
+        a.rank = (params.rep_mode == TFDP_REP_FFT) ? rank : nullptr;
         a.gin = gin;
         a.Gs = Gs;
         a.gout = gout;
@@ -233,10 +244,13 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     Arena A;
     size_t o_cnt = A.take(sizeof(int) * (size_t)scan_blocks * chunk);
     size_t o_off = A.take(sizeof(int) * ((size_t)nbox_max + 1));
-    size_t o_bsum = A.take(sizeof(int) * 1024);
+    size_t o_bsum = A.take(sizeof(unsigned long long) * 1024);  // scan tile status words
     size_t o_ks = A.take(sizeof(int2) * n);
-    size_t o_sxy = A.take(sizeof(float2) * n);
-    size_t o_perm = A.take(sizeof(int) * n);
+    size_t o_vp0 = A.take(sizeof(int) * n);
+    size_t o_vp1 = A.take(sizeof(int) * n);
+    size_t o_vx0 = A.take(sizeof(float2) * n);
+    size_t o_vx1 = A.take(sizeof(float2) * n);
+    size_t o_rank = A.take(sizeof(int) * n);
     size_t o_gin = A.take(sizeof(float) * 3 * (size_t)Gs * Gs);
     size_t o_T1 = A.take(sizeof(float2) * 3 * NH * ystride);
     size_t o_T2 = A.take(sizeof(float2) * 3 * NH * ystride);
@@ -256,8 +270,11 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->off = (int*)(b + o_off);
     g->bsum = (int*)(b + o_bsum);
     g->keyslot = (int2*)(b + o_ks);
-    g->sxy = (float2*)(b + o_sxy);
-    g->perm = (int*)(b + o_perm);
+    g->vperm[0] = (int*)(b + o_vp0);
+    g->vperm[1] = (int*)(b + o_vp1);
+    g->vxy[0] = (float2*)(b + o_vx0);
+    g->vxy[1] = (float2*)(b + o_vx1);
+    g->rank = (int*)(b + o_rank);
     g->gin = (float*)(b + o_gin);
     g->T1 = (float2*)(b + o_T1);
     g->T2 = (float2*)(b + o_T2);
@@ -276,6 +293,8 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->fft_k = g->params.k_interp;
     g->fft_grid_max = g->params.grid_max;
     CK(cudaMemsetAsync(g->cnt, 0, sizeof(int) * (size_t)scan_blocks * chunk, g->stream));
+    CK(cudaMemsetAsync(g->bsum, 0, sizeof(unsigned long long) * 1024, g->stream));
+    CK(cudaMemsetAsync(&g->dst->scan_ticket, 0, sizeof(unsigned long long), g->stream));
     CK(cudaMemsetAsync(g->gin, 0, sizeof(float) * 3 * (size_t)Gs * Gs, g->stream));
     std::vector<float2> tw(P);
     const double pi = 3.14159265358979323846;
@@ -324,6 +343,8 @@ tfdp_status refresh_bbox(tfdp_graph* g) {
     CK(cudaMemcpyAsync(&g->dst->bbox[slot][0], init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
     CK(cudaStreamSynchronize(g->stream));  // `init` is a stack buffer
     CK(launch_bbox(g->node_launch(), slot, g->stream));
+    // the caller order is the visit order after an upload (the FFT path only)
+    if (g->fft_mem && g->params.rep_mode == TFDP_REP_FFT) CK(launch_order_reset(g->node_launch(), slot, g->stream));
     return TFDP_OK;
 }
 
@@ -347,7 +368,15 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
         CK(mark());
     } else {
         const FftLaunch f = g->fft_launch();
-        CK(launch_fft_sort(a, advance, s));
+        CK(launch_fft_grid(a, advance, s));
+        // attraction on the side stream, overlapping sort, spread and FFT
+        CK(cudaEventRecord(g->fork_ev, s));
+        CK(cudaStreamWaitEvent(g->side_stream, g->fork_ev, 0));
+        if (tm) CK(cudaEventRecordWithFlags(g->ev_attract[0], g->side_stream, cudaEventRecordExternal));
+        CK(launch_attract(a, g->side_stream));
+        if (tm) CK(cudaEventRecordWithFlags(g->ev_attract[1], g->side_stream, cudaEventRecordExternal));
+        CK(cudaEventRecord(g->join_ev, g->side_stream));
+        CK(launch_fft_sort(a, s));
         CK(mark());
         CK(launch_fft_spread(a, s));
         CK(mark());
@@ -359,7 +388,8 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
         CK(mark());
         CK(launch_rows_inv(f, s));
         CK(mark());
-        CK(launch_fft_back(a, eval, s));
+        CK(cudaStreamWaitEvent(s, g->join_ev, 0));
+        CK(launch_fft_back(a, advance, eval, s));
         CK(mark());
     }
     return TFDP_OK;
@@ -367,8 +397,10 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
 
 // Kernels launched per iteration (count of the launches above).
 int kernels_per_iteration(const tfdp_graph* g) {
-    // FFT: grid + bin + 3 scan + scatter, spread, 2 spectrum, rows, cols, rows, gather + edge
-    return g->params.rep_mode == TFDP_REP_EXACT ? 2 : (6 + 1 + 2 + 1 + 1 + 1 + 2);
+    // FFT: attraction, grid + bin + scan + scatter, spread, rows, cols, rows, gather +
+    // update; two more spectrum kernels for the shared-memory FFT (P = 8192)
+    if (g->params.rep_mode == TFDP_REP_EXACT) return 2;
+    return (1 + 4 + 1 + 1 + 1 + 1 + 1) + (g->logP > 12 ? 2 : 0);
 }
 
 long long exec_key_of(const tfdp_graph* g) {
@@ -518,7 +550,14 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     g->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&g->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g->side_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->join_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+        if (g->side_stream) cudaStreamDestroy(g->side_stream);
+        if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+        if (g->join_ev) cudaEventDestroy(g->join_ev);
         delete g;
         return cuda_fail(e, "create stream");
     }
@@ -541,6 +580,9 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     e = cudaMalloc(&g->node_mem, A.bytes);
     if (e != cudaSuccess) {
         cudaStreamDestroy(g->cap_stream);
+        cudaStreamDestroy(g->side_stream);
+        cudaEventDestroy(g->fork_ev);
+        cudaEventDestroy(g->join_ev);
         delete g;
         return cuda_fail(e, "cudaMalloc(node arena)");
     }
@@ -595,10 +637,14 @@ tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
     if (!g || !p) return TFDP_ERR_INVALID_ARG;
     tfdp_status st = tfdp_params_check(p, nullptr);
     if (st != TFDP_OK) return st;
+    const bool to_fft = p->rep_mode == TFDP_REP_FFT && g->params.rep_mode != TFDP_REP_FFT;
     g->params = *p;
     if (p->rep_mode == TFDP_REP_FFT) {
+        void* before = g->fft_mem;
         st = alloc_fft(g);
         if (st != TFDP_OK) return st;
+        if ((to_fft || g->fft_mem != before) && g->n > 0)
+            CK(launch_order_reset(g->node_launch(), (int)(g->host_iter & 1), g->stream));
     }
     st = upload_params(g);
     if (st != TFDP_OK) return st;
@@ -648,6 +694,7 @@ tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
     }
     while (left-- > 0) CK(cudaGraphLaunch(g->exec1, g->stream));
     g->host_iter += iters;
+    g->last_was_eval = false;
     return TFDP_OK;
 }
 
@@ -670,6 +717,7 @@ tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_dev
     if (g->n == 0) return TFDP_OK;
     tfdp_status st = enqueue_step(g, g->stream, 0, 1);
     if (st != TFDP_OK) return st;
+    g->last_was_eval = true;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (frep) CK(cudaMemcpyAsync(frep, g->frep_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
     if (fatt) CK(cudaMemcpyAsync(fatt, g->fatt_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
@@ -701,6 +749,7 @@ tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable) {
     if (!g) return TFDP_ERR_INVALID_ARG;
     if (enable && !g->ev[0]) {
         for (int i = 0; i <= TFDP_NUM_STAGES; ++i) CK(cudaEventCreate(&g->ev[i]));
+        for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&g->ev_attract[i]));
     }
     if ((bool)enable != g->timing) {
         g->timing = enable != 0;
@@ -721,6 +770,11 @@ tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages) {
         CK(cudaEventElapsedTime(&t, g->ev[i], g->ev[i + 1]));
         if (base + i < nstages) ms[base + i] = t;
     }
+    if (g->params.rep_mode != TFDP_REP_EXACT && TFDP_STAGE_ATTRACT < nstages) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, g->ev_attract[0], g->ev_attract[1]));
+        ms[TFDP_STAGE_ATTRACT] = t;
+    }
     return TFDP_OK;
 }
 
@@ -739,6 +793,12 @@ tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
     if (g->fft_mem) cudaFree(g->fft_mem);
     if (g->node_mem) cudaFree(g->node_mem);
     if (g->step_table) cudaFree(g->step_table);
+    if (g->side_stream) cudaStreamSynchronize(g->side_stream);
+    for (int i = 0; i < 2; ++i)
+        if (g->ev_attract[i]) cudaEventDestroy(g->ev_attract[i]);
+    if (g->fork_ev) cudaEventDestroy(g->fork_ev);
+    if (g->join_ev) cudaEventDestroy(g->join_ev);
+    if (g->side_stream) cudaStreamDestroy(g->side_stream);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
     return TFDP_OK;
@@ -751,8 +811,10 @@ tfdp_status tfdp_debug_fetch(tfdp_graph* g, int what, void* dst, size_t bytes) {
     CK(cudaStreamSynchronize(g->stream));
     const size_t G = (size_t)s.grid.G;
     if (what == TFDP_DEBUG_SORT_PERM) {
-        if (!g->perm || bytes < sizeof(int) * (size_t)g->n) return TFDP_ERR_INVALID_ARG;
-        CK(cudaMemcpy(dst, g->perm, sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToHost));
+        // the latest sort wrote visit order (t & 1) ^ 1 of its iteration t
+        const int slot = g->last_was_eval ? (int)((g->host_iter & 1) ^ 1) : (int)(g->host_iter & 1);
+        if (!g->vperm[slot] || bytes < sizeof(int) * (size_t)g->n) return TFDP_ERR_INVALID_ARG;
+        CK(cudaMemcpy(dst, g->vperm[slot], sizeof(int) * (size_t)g->n, cudaMemcpyDeviceToHost));
         return TFDP_OK;
     }
     if (what == TFDP_DEBUG_CELL_START) {

@@ -18,7 +18,7 @@ PREC_FP32, PREC_BF16X3 = 0, 1
 GRID_PAPER, GRID_SNAP_H = 0, 1
 DEBUG_GRID_CHARGES, DEBUG_GRID_OUTPUT, DEBUG_SORT_PERM, DEBUG_CELL_START = 1, 2, 3, 4
 STAGES = ["sort", "spread", "spectrum", "rows_fwd", "cols", "rows_inv", "gather_update",
-          "exact", "edge_update"]
+          "exact", "edge_update", "attract"]
 
 STATUS = {0: "TFDP_OK", 1: "TFDP_ERR_INVALID_ARG", 2: "TFDP_ERR_BAD_GRAPH",
           3: "TFDP_ERR_PARAM_RANGE", 4: "TFDP_ERR_OUT_OF_MEMORY", 5: "TFDP_ERR_CUDA",
