@@ -193,6 +193,54 @@ def cpu_baseline(e, xy, spec, budget_s=15.0):
                 iters, mode, el)}
 
 
+def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48):
+    """512 mixed graphs (n log-uniform in [1k, 50k]) advanced by one persistent launch
+    per batch iteration, against the same graphs run one at a time (a sample of them)."""
+    import torch
+    from paper_2303_03964_gb300 import synth, tfdp
+    graphs = synth.batch_mixed()
+    params = [tfdp.params_default(grid_max=255, total_iters=300) for _ in graphs]
+    total_n = sum(g[0] for g in graphs)
+    b = tfdp.Batch(graphs, params, stream=stream.cuda_stream)
+    blocks = b.autotune(3)
+
+    def timed(fn):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1)
+
+    for _ in range(warmup):
+        timed(lambda: b.iterate(1))
+    ms = [timed(lambda: b.iterate(1)) for _ in range(steps)]
+    flags = max(b.stats(q)["device_flags"] for q in (0, len(graphs) // 2, len(graphs) - 1))
+    b.close()
+    # solo: a sample of the same graphs, one graph per launch sequence
+    idx = list(range(0, len(graphs), max(1, len(graphs) // solo_sample)))[:solo_sample]
+    solo_n, solo_ms = 0, 0.0
+    for q in idx:
+        n, e, xy = graphs[q]
+        with tfdp.Graph(n, e, xy, params[q], stream=stream.cuda_stream) as g:
+            for _ in range(2):
+                timed(lambda: g.iterate(1))
+            t = [timed(lambda: g.iterate(1)) for _ in range(3)]
+        solo_n += n
+        solo_ms += statistics.median(t)
+    batch_value = total_n * len(ms) / (sum(ms) * 1e-3)
+    solo_value = solo_n / (solo_ms * 1e-3)
+    return {"workload": "512 graphs, n log-uniform in [1k, 50k] (sum %d), SBM / BA m0=2 / lattice in turn, "
+                        "k=3, grid <= 255 (P=512), FP32" % total_n,
+            "value": batch_value, "unit": UNIT, "ms_per_step": statistics.fmean(ms),
+            "cooperative_ctas": blocks, "solo_value": solo_value,
+            "solo_sample": "%d of the graphs (%d nodes), one iteration each, median of 3" % (len(idx), solo_n),
+            "speedup_vs_solo": batch_value / solo_value, "device_flags": flags}
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -338,6 +386,9 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline and ws >= 1 and rank == 0:
         cpu = cpu_baseline(e, xy, spec)
+    batched = None
+    if not args.no_batch and args.workload == "lattice_1m":
+        batched = batched_measurement(args, stream, flush, args.steps, args.warmup)
     value = ws * n * args.steps / (total_ms * 1e-3)
     q = sorted(step_ms)
     line = {
@@ -351,6 +402,7 @@ def run_ours(args):
                    "parallelism": "replicas" if ws > 1 else "single"},
         "step_ms_p50": q[len(q) // 2], "step_ms_p99": q[min(len(q) - 1, int(0.99 * len(q)))],
         "mixed": None,
+        "batched": batched,
         "stages_ms": mean_stage,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -375,6 +427,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lattice_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -196,8 +196,136 @@ tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages);
 /* Wait for all work queued on the graph's stream. */
 tfdp_status tfdp_synchronize(tfdp_graph* g);
 
+/* Move the graph to another CUDA stream (waits for the work queued on the old one). */
+tfdp_status tfdp_graph_set_stream(tfdp_graph* g, void* stream);
+
+/* Device bytes tfdp_create_graph would allocate for n nodes, m edges and `params`
+ * (NULL = defaults), within a few KB; used for admission by memory footprint. */
+tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params, size_t* bytes);
+
 /* Free the graph and its device memory (synchronises first). NULL is a no-op. */
 tfdp_status tfdp_destroy_graph(tfdp_graph* g);
+
+/*
+ * Batches: many independent graphs advanced together by one cooperative persistent
+ * kernel per call (Sec. 3.4 ibFFT path for every graph; the batching itself has no
+ * counterpart in the paper). Graphs keep their own parameters, grids, spectra, state
+ * and iteration counters; the arithmetic per graph is that of a single graph, so each
+ * graph's result equals its solo run up to floating-point summation order.
+ */
+typedef struct tfdp_batch tfdp_batch;
+
+/*
+ * Create a batch of num_graphs >= 1 graphs on the current device.
+ *   n, m       per graph node and edge counts (n >= 1)
+ *   edges      per graph host pointer to 2 m int32 ids (NULL allowed when m = 0)
+ *   xy0        per graph host pointer to n x 2 FP32 initial positions
+ *   params     NULL (defaults for all) or num_graphs parameter sets; rep_mode is forced
+ *              to TFDP_REP_FFT; all graphs must share k_interp. The FFT size is the
+ *              largest any graph needs and must be <= 2048 (grid_max <= 1024), else
+ *              TFDP_ERR_PARAM_RANGE.
+ *   stream     cudaStream_t for all work of the batch
+ * Inputs are copied. Errors as for tfdp_create_graph.
+ */
+tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_t* m,
+                              const int32_t* const* edges, const float* const* xy0,
+                              const tfdp_params* params, void* stream, tfdp_batch** out);
+
+/* Run `iters` iterations of every graph in one persistent launch (replayed from a
+ * captured CUDA graph). Asynchronous on the batch's stream. */
+tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters);
+
+/* Forces of graph `graph` at the current positions (the whole batch is evaluated
+ * once, no node moves); frep / fatt n x 2 FP32, either may be NULL. Synchronises. */
+tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, float* fatt,
+                                   int on_device);
+
+/* Positions of graph `graph` (n x 2 FP32, caller order). Synchronises. */
+tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, int on_device);
+
+/* Diagnostics of graph `graph` (as tfdp_get_stats). Synchronises. */
+tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out);
+
+tfdp_status tfdp_batch_synchronize(tfdp_batch* b);
+tfdp_status tfdp_batch_destroy(tfdp_batch* b);
+
+/* CTAs of the cooperative launch (all co-resident on the device), 0 for NULL. */
+int32_t tfdp_batch_grid_blocks(const tfdp_batch* b);
+
+/* Launch-shape autotuner: times `trials` force evaluations of the whole batch for each
+ * number of co-resident CTAs per SM the kernel allows and keeps the fastest
+ * (*chosen_blocks, may be NULL, receives the CTA count). Synchronises; no node moves. */
+tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_blocks);
+
+/*
+ * Serving: interactive layout jobs with continuous batching. A job is a graph and a
+ * queue of requests: its initial layout, then updates (new alpha, beta, gamma applied
+ * to the current layout, with the step schedule restarted over the update's
+ * iterations: the warm-started re-layout of Sec. 5 "Global Refinement"). Jobs are
+ * admitted in arrival order as soon as a slot is free and their device footprint
+ * (tfdp_graph_footprint) fits the budget; admitted jobs keep positions and kernel
+ * spectra resident, each on its own stream, and a worker thread advances all of them
+ * by up to chunk_iters iterations per tick, so their kernels overlap on the device.
+ * A job's result does not depend on the other jobs (the iteration is bitwise
+ * reproducible). The batching has no counterpart in the paper.
+ */
+typedef struct tfdp_server tfdp_server;
+
+typedef struct {
+    int64_t request_id;
+    int64_t job_id;
+    int32_t kind;      /* 0: initial layout, 1: update */
+    int32_t iters;
+    double t_submit;   /* seconds since the server was created */
+    double t_start;    /* first iteration queued */
+    double t_done;     /* last iteration completed */
+    int32_t status;    /* tfdp_status of the request */
+    int32_t reserved;
+} tfdp_done;
+
+typedef struct {
+    int32_t active;          /* admitted jobs */
+    int32_t peak_active;
+    int32_t waiting;         /* submitted, not admitted yet */
+    int32_t jobs;            /* known jobs (admitted, waiting or finishing) */
+    size_t used_bytes;       /* footprint of the admitted jobs */
+    size_t budget_bytes;
+    int64_t node_iterations; /* sum over completed iterations of the job's node count */
+    int32_t reserved[8];
+} tfdp_server_stats;
+
+/* Start a server on the current device: admission budget in bytes, at most
+ * max_active admitted jobs, chunk_iters iterations per job per scheduling tick. */
+tfdp_status tfdp_server_create(size_t hbm_budget_bytes, int32_t max_active, int32_t chunk_iters,
+                               tfdp_server** out);
+
+/* Submit a job (inputs copied) whose first request lays it out for `iters` iterations
+ * with `params` (NULL = defaults). TFDP_ERR_OUT_OF_MEMORY if its footprint exceeds the
+ * whole budget. Returns its job id and the request id. Thread-safe. */
+tfdp_status tfdp_server_submit(tfdp_server* s, int64_t n, int64_t m, const int32_t* edges,
+                               const float* xy0, const tfdp_params* params, int32_t iters,
+                               int64_t* job_id, int64_t* request_id);
+
+/* Queue an update of a job: `params` (same k_interp, grid_max and rep_mode as the job)
+ * with the step schedule restarted over `iters` iterations. Thread-safe. */
+tfdp_status tfdp_server_update(tfdp_server* s, int64_t job_id, const tfdp_params* params,
+                               int32_t iters, int64_t* request_id);
+
+/* Take up to `max` completed requests (oldest first); waits up to wait_ms for one. */
+tfdp_status tfdp_server_poll(tfdp_server* s, tfdp_done* out, int32_t max, int32_t* count,
+                             int32_t wait_ms);
+
+/* Positions of an admitted job with no request pending (n x 2 FP32, caller order);
+ * TFDP_ERR_BUSY while it has work queued. */
+tfdp_status tfdp_server_get_positions(tfdp_server* s, int64_t job_id, float* xy);
+
+/* Free the job's slot and memory once its queued requests are done. */
+tfdp_status tfdp_server_release(tfdp_server* s, int64_t job_id);
+
+tfdp_status tfdp_server_get_stats(tfdp_server* s, tfdp_server_stats* out);
+
+/* Stop the worker threads and free every job. */
+tfdp_status tfdp_server_destroy(tfdp_server* s);
 
 /*
  * Exact repulsion without any device allocation, for callers that cannot allocate:

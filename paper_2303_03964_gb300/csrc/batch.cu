@@ -1,0 +1,892 @@
+// batch.cu -- many graphs advanced together by one cooperative persistent kernel.
+//
+// A batch holds B independent graphs in packed arenas (positions, CSR, sort buffers)
+// with per-graph parameters, state, grids and spectra. tfdp_batch_iterate runs `iters`
+// t-FDP iterations of every graph in a single launch: the kernel walks through the
+// nine phases of an iteration (grid policy; binning + attraction; per-graph scan;
+// scatter; spread; row / column / inverse-row FFT stages; back-projection + update),
+// each phase distributing (graph, item) work over all CTAs, with a grid-wide barrier
+// between phases. The per-node and per-transform arithmetic is the single-graph code
+// (node_dev.cuh, fft_stages.cuh), so every graph evolves as it would alone.
+//
+// All graphs of a batch share k and the FFT size P (the largest any graph needs:
+// P >= 2 G_max - 1 for every graph, so each graph's linear convolution is exact).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/tfdp.h"
+#include "common.cuh"
+#include "fft_stages.cuh"
+#include "node_dev.cuh"
+
+namespace cg = cooperative_groups;
+using namespace tfdp;
+
+namespace {
+
+constexpr int kBThreads = 256;   // threads per CTA in every phase
+constexpr int kBChunk = 256;     // nodes / boxes per work item
+
+// Per-graph geometry and buffers (device copy).
+struct BGraph {
+    int n, node_off, rowptr_off, col_off;
+    int G_max, Gs, ystride, nbox_max;
+    int* cnt;
+    int* off;
+    float* gin;
+    float2* T1;
+    float2* T2;
+    float4* gout;
+    float2* S1;
+    float* specK;
+    float* specHx;
+    float* specHy;
+};
+
+struct BatchArgs {
+    int B;
+    const BGraph* graphs;
+    DevState* st;           // [B]
+    const DevParams* prm;   // [B]
+    float2* xy[2];          // packed caller-order positions (global node index)
+    float2* vxy[2];         // packed visit orders (see launch.h NodeLaunch)
+    int* vperm[2];          // global node ids
+    int* rank;              // global sorted slot of each node
+    int2* keyslot;
+    float2* fatt;
+    float2* frep;
+    const int* rowptr;      // per graph n + 1 entries (local offsets into its col range)
+    const int* col;         // global node ids
+    const float2* tw;
+    const int* pre_nodes;   // [B + 1] prefix of node chunks
+    const int* pre_boxes;   // [B + 1] prefix of box chunks (nbox_max)
+    const int* pre_rows;    // [B + 1] prefix of row blocks (data + spectrum)
+    const int* pre_cols;    // [B + 1] prefix of column blocks
+    int iters;
+    int advance;
+    int eval;
+};
+
+// graph owning global item `it` of a phase with prefix table pre[0..B]
+__device__ __forceinline__ int owner(const int* __restrict__ pre, int B, int it) {
+    int lo = 0, hi = B;  // pre[lo] <= it < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int LOGP, int K>
+__global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
+    using Rg = RegGeom<LOGP>;
+    extern __shared__ float2 sm[];
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < a.iters; ++it) {
+        // ---- phase 0: grid policy, step and spectrum key of every graph
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.B; g += gridDim.x * blockDim.x)
+            grid_decide(a.st + g, a.prm[g], a.advance);
+        grid.sync();
+
+        // ---- phase 1: binning (visit order) and attraction (caller order)
+        const int n_node_items = __ldg(a.pre_nodes + a.B);
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
+            if (v < G.n) {
+                const int gv = G.node_off + v;
+                const float2 p = a.vxy[cur][gv];
+                float tq;
+                const int bx = box_of(p.x, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
+                const int by = box_of(p.y, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
+                const int key = by * st->grid.n_int + bx;
+                const unsigned active = __activemask();
+                const unsigned same = __match_any_sync(active, key);
+                const int leader = __ffs(same) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(G.cnt + key, __popc(same));
+                base = __shfl_sync(same, base, leader);
+                a.keyslot[gv] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
+                // attraction of caller-order node gv (rowptr holds local offsets)
+                const float2 pi = a.xy[cur][gv];
+                a.fatt[gv] = attraction(v, pi, a.rowptr + G.rowptr_off, a.col + G.col_off, a.xy[cur],
+                                        (float)a.prm[g].alpha, (float)a.prm[g].beta);
+            }
+        }
+        grid.sync();
+
+        // ---- phase 2: exclusive scan of each graph's box counts (one CTA per graph)
+        for (int g = blockIdx.x; g < a.B; g += gridDim.x) {
+            const BGraph G = a.graphs[g];
+            const int nbox = a.st[g].grid.n_int * a.st[g].grid.n_int;
+            __shared__ int s_w[32];
+            __shared__ int s_carry;
+            if (threadIdx.x == 0) s_carry = 0;
+            __syncthreads();
+            for (int c0 = 0; c0 < nbox; c0 += kBThreads * 8) {
+                const int i0 = c0 + threadIdx.x * 8;
+                int v[8], tsum = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    v[q] = (i0 + q < nbox) ? G.cnt[i0 + q] : 0;
+                    tsum += v[q];
+                }
+                int incl = tsum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int w = threadIdx.x >> 5;
+                if (lane == 31) s_w[w] = incl;
+                __syncthreads();
+                if (w == 0) {
+                    const int x = lane < (kBThreads >> 5) ? s_w[lane] : 0;
+                    int xi = x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, xi, o);
+                        if (lane >= o) xi += y;
+                    }
+                    if (lane < (kBThreads >> 5)) s_w[lane] = xi - x;
+                }
+                __syncthreads();
+                int run = s_carry + s_w[w] + incl - tsum;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (i0 + q < nbox) {
+                        G.off[i0 + q] = run;
+                        G.cnt[i0 + q] = 0;
+                    }
+                    run += v[q];
+                }
+                __syncthreads();
+                if (threadIdx.x == kBThreads - 1) s_carry = run;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) G.off[nbox] = G.n;
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 3: scatter into the new cell-sorted order
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
+            if (v < G.n) {
+                const int gv = G.node_off + v;
+                const int2 ks = a.keyslot[gv];
+                const int pos = G.off[ks.x] + ks.y;
+                const int i = a.vperm[cur][gv];
+                if ((unsigned)pos >= (unsigned)G.n || i < G.node_off || i >= G.node_off + G.n) {
+                    atomicOr(&st->flags, FLAG_SORT_RANGE);
+                } else {
+                    a.vxy[cur ^ 1][G.node_off + pos] = a.vxy[cur][gv];
+                    a.vperm[cur ^ 1][G.node_off + pos] = i;
+                    a.rank[i] = G.node_off + pos;
+                }
+            }
+        }
+        grid.sync();
+
+        // ---- phase 4: spread, one thread per box
+        const int n_box_items = __ldg(a.pre_boxes + a.B);
+        for (int item = blockIdx.x; item < n_box_items; item += gridDim.x) {
+            const int g = owner(a.pre_boxes, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const GridDesc gd = st->grid;
+            const int b = (item - __ldg(a.pre_boxes + g)) * kBChunk + threadIdx.x;
+            if (b < gd.n_int * gd.n_int) {
+                const int by = b / gd.n_int;
+                const int bx = b - by * gd.n_int;
+                const float2* sxy = a.vxy[(int)(st->t_cur & 1) ^ 1] + G.node_off;
+                spread_box<K>(sxy, max(G.off[b], 0), min(G.off[b + 1], G.n), bx, by, axis_geom(gd), G.gin, G.Gs);
+            }
+        }
+        grid.sync();
+
+        // ---- phase 5: forward row transforms (and kernel-sample rows on a rebuild)
+        const int n_row_items = __ldg(a.pre_rows + a.B);
+        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
+            const int g = owner(a.pre_rows, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const int blk = item - __ldg(a.pre_rows + g);
+            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+            if (blk < data_blocks) {
+                GridSource gs;
+                gs.gin = G.gin;
+                gs.Gs = G.Gs;
+                rows_fwd_body<LOGP>(gs, st->grid.G, blk, G.T1, G.ystride, a.tw, sm);
+            } else if (st->spec_dirty) {
+                KernelSource ks;
+                ks.P = 1 << LOGP;
+                ks.bind(st, a.prm + g);
+                rows_fwd_body<LOGP>(ks, ks.P, blk - data_blocks, G.S1, 1 << LOGP, a.tw, sm);
+            }
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 6: column transforms, spectral product (spectrum rebuilt if needed)
+        const int n_col_items = __ldg(a.pre_cols + a.B);
+        for (int item = blockIdx.x; item < n_col_items; item += gridDim.x) {
+            const int g = owner(a.pre_cols, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            cols_body<LOGP>(item - __ldg(a.pre_cols + g), G.T1, G.T2, G.ystride, G.specK, G.specHx, G.specHy, G.S1,
+                            a.tw, st->grid.G, st->spec_dirty, sm);
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 7: inverse row transforms into (A, O^x, O^y)
+        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
+            const int g = owner(a.pre_rows, a.B, item);
+            const BGraph G = a.graphs[g];
+            const int blk = item - __ldg(a.pre_rows + g);
+            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+            if (blk < data_blocks) rows_inv_body<LOGP>(blk, G.T2, G.ystride, G.gout, G.Gs, a.tw, a.st[g].grid.G, sm);
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 8: back-projection + update in sorted order
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int nxt = cur ^ 1;
+            const int chunk = item - __ldg(a.pre_nodes + g);
+            const int s = chunk * kBChunk + threadIdx.x;
+            float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
+            unsigned bad = 0;
+            if (s < G.n) {
+                const int gs = G.node_off + s;
+                const float2 p = a.vxy[nxt][gs];
+                const int i = a.vperm[nxt][gs];
+                if (i >= G.node_off && i < G.node_off + G.n) {
+                    const float2 fr = gather_frep<K>(p, axis_geom(st->grid), G.gout, G.Gs);
+                    sfx = fr.x;
+                    sfy = fr.y;
+                    if (a.eval) {
+                        a.frep[i] = fr;
+                    } else {
+                        const float2 fa = a.fatt[i];
+                        const float2 q = capped_step(p, make_float2(fr.x + fa.x, fr.y + fa.y), (float)st->step_cur);
+                        if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+                        a.xy[nxt][i] = q;
+                        a.vxy[nxt][gs] = q;
+                        mn = fminf(q.x, q.y);
+                        mx = fmaxf(q.x, q.y);
+                    }
+                }
+            }
+            if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+            // per-chunk reduction; every chunk lies inside one graph
+            __shared__ float s_mn[kBThreads / 32], s_mx[kBThreads / 32], s_fx[kBThreads / 32], s_fy[kBThreads / 32];
+            mn = warp_min(mn);
+            mx = warp_max(mx);
+            sfx = warp_sumf(sfx);
+            sfy = warp_sumf(sfy);
+            const int w = threadIdx.x >> 5;
+            if (lane == 0) {
+                s_mn[w] = mn;
+                s_mx[w] = mx;
+                s_fx[w] = sfx;
+                s_fy[w] = sfy;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double fx = 0.0, fy = 0.0;
+                for (int q = 0; q < kBThreads / 32; ++q) {
+                    mn = fminf(mn, s_mn[q]);
+                    mx = fmaxf(mx, s_mx[q]);
+                    fx += s_fx[q];
+                    fy += s_fy[q];
+                }
+                if (!a.eval && mn <= mx) {
+                    atomicMin(&st->bbox[nxt][0], f2ord(mn));
+                    atomicMax(&st->bbox[nxt][1], f2ord(mx));
+                }
+                atomicAdd(&st->net_frep[0], fx);
+                atomicAdd(&st->net_frep[1], fy);
+                if (chunk == 0 && !a.eval && a.advance) st->iter = st->t_cur + 1;
+            }
+            __syncthreads();
+        }
+        grid.sync();
+    }
+}
+
+// Visit order := caller order for every graph (after a position upload).
+__global__ void k_batch_order_reset(int N, const float2* __restrict__ xy, float2* vxy, int* vperm) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+        vperm[v] = v;
+        vxy[v] = xy[v];
+    }
+}
+
+// bbox of each graph into its slot (positions xy, graph of each chunk by prefix table).
+__global__ void k_batch_bbox(BatchArgs a, int slot) {
+    const int n_node_items = __ldg(a.pre_nodes + a.B);
+    for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+        const int g = owner(a.pre_nodes, a.B, item);
+        const BGraph G = a.graphs[g];
+        const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
+        float mn = INFINITY, mx = -INFINITY;
+        if (v < G.n) {
+            const float2 p = a.xy[slot][G.node_off + v];
+            mn = fminf(p.x, p.y);
+            mx = fmaxf(p.x, p.y);
+        }
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if ((threadIdx.x & 31) == 0 && mn <= mx) {
+            atomicMin(&a.st[g].bbox[slot][0], f2ord(mn));
+            atomicMax(&a.st[g].bbox[slot][1], f2ord(mx));
+        }
+    }
+}
+
+thread_local std::string b_err;
+
+tfdp_status bfail(cudaError_t e, const char* where) {
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    b_err = buf;
+    return e == cudaErrorMemoryAllocation ? TFDP_ERR_OUT_OF_MEMORY : TFDP_ERR_CUDA;
+}
+
+#define BK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return bfail(e_, #call);       \
+    } while (0)
+
+size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int log2c(long long v) {
+    int l = 0;
+    while ((1LL << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct tfdp_batch {
+    int B = 0;
+    int64_t N = 0, M = 0;
+    int k = 3, logP = 9, P = 512;
+    cudaStream_t stream = nullptr;
+    std::vector<tfdp_params> params;
+    std::vector<int64_t> n, node_off;
+    std::vector<BGraph> hg;
+    int64_t host_iter = 0;
+    void* mem = nullptr;       // node + FFT arena
+    BatchArgs args{};
+    BGraph* d_graphs = nullptr;
+    DevState* d_st = nullptr;
+    DevParams* d_prm = nullptr;
+    double* d_steps = nullptr;  // per-graph step tables, B x T_max
+    int T_max = 0;
+    int grid_blocks = 0;       // cooperative grid size
+    cudaGraphExec_t exec = nullptr;
+    int exec_iters = -1;
+    bool no_graph = false;
+};
+
+namespace {
+
+template <int LOGP, int K>
+cudaError_t batch_launch_t(const BatchArgs& a, int blocks, cudaStream_t s) {
+    using Rg = RegGeom<LOGP>;
+    const size_t smem = std::max(Rg::rows_smem, Rg::cols_smem);  // attribute set at creation
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch<LOGP, K>, a);
+}
+
+template <int LOGP, int K>
+cudaError_t batch_occupancy_t(int* blocks_per_sm) {
+    using Rg = RegGeom<LOGP>;
+    const size_t smem = std::max(Rg::rows_smem, Rg::cols_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batch<LOGP, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<LOGP, K>, kBThreads, smem);
+}
+
+// RegGeom<LOGP>::T * CG must equal kBThreads for the FFT phases: P in [128, 2048].
+#define TFDP_BATCH_DISPATCH(FN, ...)                               \
+    switch (b->logP * 4 + b->k) {                                  \
+        case 7 * 4 + 1: return FN<7, 1>(__VA_ARGS__);              \
+        case 7 * 4 + 2: return FN<7, 2>(__VA_ARGS__);              \
+        case 7 * 4 + 3: return FN<7, 3>(__VA_ARGS__);              \
+        case 8 * 4 + 1: return FN<8, 1>(__VA_ARGS__);              \
+        case 8 * 4 + 2: return FN<8, 2>(__VA_ARGS__);              \
+        case 8 * 4 + 3: return FN<8, 3>(__VA_ARGS__);              \
+        case 9 * 4 + 1: return FN<9, 1>(__VA_ARGS__);              \
+        case 9 * 4 + 2: return FN<9, 2>(__VA_ARGS__);              \
+        case 9 * 4 + 3: return FN<9, 3>(__VA_ARGS__);              \
+        case 10 * 4 + 1: return FN<10, 1>(__VA_ARGS__);            \
+        case 10 * 4 + 2: return FN<10, 2>(__VA_ARGS__);            \
+        case 10 * 4 + 3: return FN<10, 3>(__VA_ARGS__);            \
+        case 11 * 4 + 1: return FN<11, 1>(__VA_ARGS__);            \
+        case 11 * 4 + 2: return FN<11, 2>(__VA_ARGS__);            \
+        case 11 * 4 + 3: return FN<11, 3>(__VA_ARGS__);            \
+        default: return cudaErrorInvalidValue;                     \
+    }
+
+cudaError_t batch_launch(const tfdp_batch* b, const BatchArgs& a, cudaStream_t s) {
+    TFDP_BATCH_DISPATCH(batch_launch_t, a, b->grid_blocks, s)
+}
+cudaError_t batch_occupancy(const tfdp_batch* b, int* bps) { TFDP_BATCH_DISPATCH(batch_occupancy_t, bps) }
+
+tfdp_status upload_batch_params(tfdp_batch* b) {
+    std::vector<DevParams> dp((size_t)b->B);
+    std::vector<double> steps((size_t)b->B * b->T_max, 0.0);
+    for (int g = 0; g < b->B; ++g) {
+        const tfdp_params& p = b->params[(size_t)g];
+        DevParams& d = dp[(size_t)g];
+        d.alpha = p.alpha;
+        d.beta = p.beta;
+        d.gamma = p.gamma;
+        d.step0 = p.step0;
+        d.step_min = p.step_min;
+        d.k = p.k_interp;
+        d.n_int_min = p.n_int_min;
+        d.grid_max = p.grid_max;
+        d.policy = p.grid_policy;
+        d.total_iters = p.total_iters;
+        d.P = b->P;
+        d.log2P = b->logP;
+        const double r = std::floor(p.gamma + 0.5);
+        d.gamma_int = (p.gamma == r && r >= 2.0 && r <= 8.0) ? (int)r : 0;
+        d.step_table = b->d_steps + (size_t)g * b->T_max;
+        const int T = p.total_iters;
+        for (int t = 0; t < T; ++t)
+            steps[(size_t)g * b->T_max + t] =
+                (T <= 1) ? p.step0 : p.step0 * std::pow(p.step_min / p.step0, (double)t / (double)(T - 1));
+    }
+    BK(cudaMemcpyAsync(b->d_prm, dp.data(), sizeof(DevParams) * b->B, cudaMemcpyHostToDevice, b->stream));
+    BK(cudaMemcpyAsync(b->d_steps, steps.data(), sizeof(double) * steps.size(), cudaMemcpyHostToDevice, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return TFDP_OK;
+}
+
+tfdp_status batch_refresh(tfdp_batch* b) {
+    const int slot = (int)(b->host_iter & 1);
+    for (int g = 0; g < b->B; ++g) {
+        const unsigned init[2] = {kOrdMinInit, kOrdMaxInit};
+        BK(cudaMemcpyAsync(&b->d_st[g].bbox[slot][0], init, sizeof(init), cudaMemcpyHostToDevice, b->stream));
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    k_batch_bbox<<<1024, kBChunk, 0, b->stream>>>(b->args, slot);
+    BK(cudaGetLastError());
+    if (b->N > 0) {
+        k_batch_order_reset<<<1024, 256, 0, b->stream>>>((int)b->N, b->args.xy[slot], b->args.vxy[slot],
+                                                        b->args.vperm[slot]);
+        BK(cudaGetLastError());
+    }
+    return TFDP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_t* m, const int32_t* const* edges,
+                              const float* const* xy0, const tfdp_params* params, void* stream, tfdp_batch** out) {
+    if (!out || num_graphs < 1 || !n || !m || !edges || !xy0) return TFDP_ERR_INVALID_ARG;
+    tfdp_batch* b = new (std::nothrow) tfdp_batch();
+    if (!b) return TFDP_ERR_OUT_OF_MEMORY;
+    b->B = num_graphs;
+    b->stream = (cudaStream_t)stream;
+    b->params.resize((size_t)num_graphs);
+    int G_need = 0;
+    for (int g = 0; g < num_graphs; ++g) {
+        tfdp_params p;
+        if (params) p = params[g];
+        else tfdp_params_default(&p);
+        p.rep_mode = TFDP_REP_FFT;
+        tfdp_status st = tfdp_params_check(&p, nullptr);
+        if (st != TFDP_OK || (g > 0 && p.k_interp != b->params[0].k_interp) || n[g] < 1 || m[g] < 0 ||
+            (m[g] > 0 && !edges[g]) || !xy0[g]) {
+            delete b;
+            return st != TFDP_OK ? st : TFDP_ERR_INVALID_ARG;
+        }
+        b->params[(size_t)g] = p;
+        G_need = std::max(G_need, (p.grid_max / p.k_interp) * p.k_interp);
+        b->T_max = std::max(b->T_max, p.total_iters);
+    }
+    b->k = b->params[0].k_interp;
+    b->logP = std::max(7, log2c(2LL * G_need - 1));
+    if (b->logP > 11) {  // one CTA of 256 threads per FFT work item: P <= 2048
+        delete b;
+        return TFDP_ERR_PARAM_RANGE;
+    }
+    b->P = 1 << b->logP;
+
+    // host CSR per graph (validated), packed with global column ids
+    b->n.assign(n, n + num_graphs);
+    b->node_off.resize((size_t)num_graphs + 1);
+    b->node_off[0] = 0;
+    for (int g = 0; g < num_graphs; ++g) b->node_off[(size_t)g + 1] = b->node_off[(size_t)g] + n[g];
+    b->N = b->node_off[(size_t)num_graphs];
+    std::vector<int> rowptr, col;
+    rowptr.reserve((size_t)(b->N + num_graphs));
+    std::vector<int> rowptr_off((size_t)num_graphs), col_off((size_t)num_graphs);
+    for (int g = 0; g < num_graphs; ++g) {
+        const int64_t ng = n[g], mg = m[g];
+        std::vector<int64_t> keys((size_t)mg);
+        std::vector<int> deg((size_t)ng, 0);
+        for (int64_t q = 0; q < mg; ++q) {
+            const int64_t u = edges[g][2 * q], v = edges[g][2 * q + 1];
+            if (u < 0 || v < 0 || u >= ng || v >= ng || u == v) {
+                delete b;
+                return TFDP_ERR_BAD_GRAPH;
+            }
+            keys[(size_t)q] = std::min(u, v) * ng + std::max(u, v);
+            deg[(size_t)u]++;
+            deg[(size_t)v]++;
+        }
+        std::sort(keys.begin(), keys.end());
+        for (size_t q = 1; q < keys.size(); ++q)
+            if (keys[q] == keys[q - 1]) {
+                delete b;
+                return TFDP_ERR_BAD_GRAPH;
+            }
+        rowptr_off[(size_t)g] = (int)rowptr.size();
+        col_off[(size_t)g] = (int)col.size();
+        const size_t r0 = rowptr.size();
+        rowptr.push_back(0);
+        for (int64_t i = 0; i < ng; ++i) rowptr.push_back(rowptr.back() + deg[(size_t)i]);
+        const size_t c0 = col.size();
+        col.resize(c0 + (size_t)(2 * mg));
+        std::vector<int> fill(rowptr.begin() + (long)r0, rowptr.end() - 1);
+        const int base = (int)b->node_off[(size_t)g];
+        for (int64_t q = 0; q < mg; ++q) {
+            const int u = edges[g][2 * q], v = edges[g][2 * q + 1];
+            col[c0 + (size_t)fill[(size_t)u]++] = base + v;
+            col[c0 + (size_t)fill[(size_t)v]++] = base + u;
+        }
+        for (int64_t i = 0; i < ng; ++i)
+            std::sort(col.begin() + (long)c0 + rowptr[r0 + (size_t)i], col.begin() + (long)c0 + rowptr[r0 + (size_t)i + 1]);
+        b->M += mg;
+    }
+
+    // item prefix tables and per-graph FFT geometry
+    const int T_fft = b->P / 8;
+    const int RG = (T_fft >= 256) ? 1 : 256 / T_fft;
+    const int CG = RG;
+    std::vector<int> pre_nodes(1, 0), pre_boxes(1, 0), pre_rows(1, 0), pre_cols(1, 0);
+    b->hg.resize((size_t)num_graphs);
+    size_t fft_bytes = 0;
+    std::vector<size_t> fft_off((size_t)num_graphs);
+    const size_t NH = (size_t)b->P / 2 + 1;
+    for (int g = 0; g < num_graphs; ++g) {
+        const tfdp_params& p = b->params[(size_t)g];
+        BGraph& G = b->hg[(size_t)g];
+        const int n_int_max = p.grid_max / p.k_interp;
+        G.n = (int)n[g];
+        G.node_off = (int)b->node_off[(size_t)g];
+        G.rowptr_off = rowptr_off[(size_t)g];
+        G.col_off = col_off[(size_t)g];
+        G.G_max = n_int_max * p.k_interp;
+        G.Gs = (int)up((size_t)G.G_max, 4);
+        G.ystride = (int)up((size_t)G.G_max, 32);
+        G.nbox_max = n_int_max * n_int_max;
+        pre_nodes.push_back(pre_nodes.back() + (G.n + kBChunk - 1) / kBChunk);
+        pre_boxes.push_back(pre_boxes.back() + (G.nbox_max + kBChunk - 1) / kBChunk);
+        pre_rows.push_back(pre_rows.back() + (G.G_max + 2 * RG - 1) / (2 * RG) + b->P / (2 * RG));
+        pre_cols.push_back(pre_cols.back() + (int)((NH + CG - 1) / CG));
+        fft_off[(size_t)g] = fft_bytes;
+        fft_bytes += up(sizeof(int) * (size_t)G.nbox_max, 256) + up(sizeof(int) * ((size_t)G.nbox_max + 1), 256) +
+                     up(sizeof(float) * 3 * (size_t)G.Gs * G.Gs, 256) + 2 * up(sizeof(float2) * 3 * NH * G.ystride, 256) +
+                     up(sizeof(float4) * (size_t)G.Gs * G.Gs, 256) + up(sizeof(float2) * 3 * NH * b->P, 256) +
+                     3 * up(sizeof(float) * NH * b->P, 256);
+    }
+    // node arena layout
+    const size_t N = (size_t)b->N;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = up(off, 256);
+        off = o + up(bytes ? bytes : 1, 256);
+        return o;
+    };
+    const size_t o_xy0 = take(sizeof(float2) * N), o_xy1 = take(sizeof(float2) * N);
+    const size_t o_vx0 = take(sizeof(float2) * N), o_vx1 = take(sizeof(float2) * N);
+    const size_t o_vp0 = take(sizeof(int) * N), o_vp1 = take(sizeof(int) * N);
+    const size_t o_rank = take(sizeof(int) * N), o_ks = take(sizeof(int2) * N);
+    const size_t o_fatt = take(sizeof(float2) * N), o_frep = take(sizeof(float2) * N);
+    const size_t o_rp = take(sizeof(int) * rowptr.size()), o_col = take(sizeof(int) * std::max<size_t>(col.size(), 1));
+    const size_t o_tw = take(sizeof(float2) * b->P);
+    const size_t o_graphs = take(sizeof(BGraph) * num_graphs), o_st = take(sizeof(DevState) * num_graphs);
+    const size_t o_prm = take(sizeof(DevParams) * num_graphs);
+    const size_t o_steps = take(sizeof(double) * (size_t)num_graphs * b->T_max);
+    const size_t o_pn = take(sizeof(int) * (num_graphs + 1)), o_pb = take(sizeof(int) * (num_graphs + 1));
+    const size_t o_pr = take(sizeof(int) * (num_graphs + 1)), o_pc = take(sizeof(int) * (num_graphs + 1));
+    const size_t o_fft = take(fft_bytes);
+    cudaError_t e = cudaMalloc(&b->mem, off);
+    if (e != cudaSuccess) {
+        delete b;
+        return bfail(e, "cudaMalloc(batch arena)");
+    }
+    char* base = (char*)b->mem;
+    BatchArgs& a = b->args;
+    a.B = num_graphs;
+    a.xy[0] = (float2*)(base + o_xy0);
+    a.xy[1] = (float2*)(base + o_xy1);
+    a.vxy[0] = (float2*)(base + o_vx0);
+    a.vxy[1] = (float2*)(base + o_vx1);
+    a.vperm[0] = (int*)(base + o_vp0);
+    a.vperm[1] = (int*)(base + o_vp1);
+    a.rank = (int*)(base + o_rank);
+    a.keyslot = (int2*)(base + o_ks);
+    a.fatt = (float2*)(base + o_fatt);
+    a.frep = (float2*)(base + o_frep);
+    a.rowptr = (const int*)(base + o_rp);
+    a.col = (const int*)(base + o_col);
+    a.tw = (const float2*)(base + o_tw);
+    b->d_graphs = (BGraph*)(base + o_graphs);
+    b->d_st = (DevState*)(base + o_st);
+    b->d_prm = (DevParams*)(base + o_prm);
+    b->d_steps = (double*)(base + o_steps);
+    a.graphs = b->d_graphs;
+    a.st = b->d_st;
+    a.prm = b->d_prm;
+    a.pre_nodes = (const int*)(base + o_pn);
+    a.pre_boxes = (const int*)(base + o_pb);
+    a.pre_rows = (const int*)(base + o_pr);
+    a.pre_cols = (const int*)(base + o_pc);
+    for (int g = 0; g < num_graphs; ++g) {
+        BGraph& G = b->hg[(size_t)g];
+        char* f = base + o_fft + fft_off[(size_t)g];
+        size_t fo = 0;
+        auto sub = [&](size_t bytes) {
+            char* q = f + fo;
+            fo += up(bytes, 256);
+            return q;
+        };
+        G.cnt = (int*)sub(sizeof(int) * (size_t)G.nbox_max);
+        G.off = (int*)sub(sizeof(int) * ((size_t)G.nbox_max + 1));
+        G.gin = (float*)sub(sizeof(float) * 3 * (size_t)G.Gs * G.Gs);
+        G.T1 = (float2*)sub(sizeof(float2) * 3 * NH * G.ystride);
+        G.T2 = (float2*)sub(sizeof(float2) * 3 * NH * G.ystride);
+        G.gout = (float4*)sub(sizeof(float4) * (size_t)G.Gs * G.Gs);
+        G.S1 = (float2*)sub(sizeof(float2) * 3 * NH * b->P);
+        G.specK = (float*)sub(sizeof(float) * NH * b->P);
+        G.specHx = (float*)sub(sizeof(float) * NH * b->P);
+        G.specHy = (float*)sub(sizeof(float) * NH * b->P);
+    }
+    auto fail = [&](tfdp_status s) {
+        tfdp_batch_destroy(b);
+        return s;
+    };
+    std::vector<float2> tw((size_t)b->P);
+    for (int t = 0; t < b->P; ++t) {
+        const double ang = -2.0 * 3.14159265358979323846 * (double)t / (double)b->P;
+        tw[(size_t)t] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    std::vector<float2> xy(N);
+    for (int g = 0; g < num_graphs; ++g)
+        std::memcpy(xy.data() + b->node_off[(size_t)g], xy0[g], sizeof(float2) * (size_t)n[g]);
+    cudaStream_t s = b->stream;
+    if ((e = cudaMemsetAsync(b->mem, 0, off, s)) != cudaSuccess) return fail(bfail(e, "memset"));
+    if ((e = cudaMemcpyAsync(a.xy[0], xy.data(), sizeof(float2) * N, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void*)a.rowptr, rowptr.data(), sizeof(int) * rowptr.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (!col.empty() && (e = cudaMemcpyAsync((void*)a.col, col.data(), sizeof(int) * col.size(), cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+        (e = cudaMemcpyAsync((void*)a.tw, tw.data(), sizeof(float2) * b->P, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(b->d_graphs, b->hg.data(), sizeof(BGraph) * num_graphs, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void*)a.pre_nodes, pre_nodes.data(), sizeof(int) * (num_graphs + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void*)a.pre_boxes, pre_boxes.data(), sizeof(int) * (num_graphs + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void*)a.pre_rows, pre_rows.data(), sizeof(int) * (num_graphs + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((void*)a.pre_cols, pre_cols.data(), sizeof(int) * (num_graphs + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return fail(bfail(e, "batch upload"));
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(bfail(e, "batch upload sync"));
+    tfdp_status st = upload_batch_params(b);
+    if (st != TFDP_OK) return fail(st);
+    int bps = 0;
+    if ((e = batch_occupancy(b, &bps)) != cudaSuccess || bps < 1) return fail(bfail(e, "batch occupancy"));
+    int sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    b->grid_blocks = bps * sms;
+    st = batch_refresh(b);
+    if (st != TFDP_OK) return fail(st);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(bfail(e, "batch init"));
+    *out = b;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters) {
+    if (!b || iters < 0) return TFDP_ERR_INVALID_ARG;
+    if (iters == 0) return TFDP_OK;
+    if (b->no_graph) {  // the cooperative launch could not be captured: launch directly
+        BatchArgs a = b->args;
+        a.iters = iters;
+        a.advance = 1;
+        a.eval = 0;
+        BK(batch_launch(b, a, b->stream));
+        b->host_iter += iters;
+        return TFDP_OK;
+    }
+    if (!b->exec || b->exec_iters != iters) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+        cudaStream_t cap;
+        BK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        BatchArgs a = b->args;
+        a.iters = iters;
+        a.advance = 1;
+        a.eval = 0;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = batch_launch(b, a, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        if (e != cudaSuccess) {
+            cudaGetLastError();  // clear the capture error, fall back to direct launches
+            b->no_graph = true;
+            return tfdp_batch_iterate(b, iters);
+        }
+        b->exec_iters = iters;
+    }
+    BK(cudaGraphLaunch(b->exec, b->stream));
+    b->host_iter += iters;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, float* fatt, int on_device) {
+    if (!b || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    BatchArgs a = b->args;
+    a.iters = 1;
+    a.advance = 0;
+    a.eval = 1;
+    BK(batch_launch(b, a, b->stream));
+    const size_t o = (size_t)b->node_off[(size_t)graph], ng = (size_t)b->n[(size_t)graph];
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (frep) BK(cudaMemcpyAsync(frep, a.frep + o, sizeof(float2) * ng, kind, b->stream));
+    if (fatt) BK(cudaMemcpyAsync(fatt, a.fatt + o, sizeof(float2) * ng, kind, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, int on_device) {
+    if (!b || !xy || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    const int slot = (int)(b->host_iter & 1);
+    BK(cudaMemcpyAsync(xy, b->args.xy[slot] + b->node_off[(size_t)graph], sizeof(float2) * (size_t)b->n[(size_t)graph],
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) {
+    if (!b || !out || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    DevState s;
+    BK(cudaMemcpyAsync(&s, b->d_st + graph, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
+    BK(cudaStreamSynchronize(b->stream));
+    std::memset(out, 0, sizeof(*out));
+    out->iteration = s.iter;
+    out->net_frep[0] = s.net_frep[0];
+    out->net_frep[1] = s.net_frep[1];
+    out->grid_lo = s.grid.lo;
+    out->grid_h = s.grid.h;
+    out->grid_n_int = s.grid.n_int;
+    out->grid_G = s.grid.G;
+    out->fft_P = b->P;
+    out->spectrum_builds = s.spec_builds;
+    out->device_flags = (int32_t)s.flags;
+    out->kernels_per_iteration = 0;  // all iterations of a call share one launch
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_synchronize(tfdp_batch* b) {
+    if (!b) return TFDP_ERR_INVALID_ARG;
+    BK(cudaStreamSynchronize(b->stream));
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_destroy(tfdp_batch* b) {
+    if (!b) return TFDP_OK;
+    if (b->mem) cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
+    return TFDP_OK;
+}
+
+int32_t tfdp_batch_grid_blocks(const tfdp_batch* b) { return b ? b->grid_blocks : 0; }
+
+tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_blocks) {
+    if (!b || trials < 1) return TFDP_ERR_INVALID_ARG;
+    int bps = 0, sms = 0, dev = 0;
+    BK(batch_occupancy(b, &bps));
+    BK(cudaGetDevice(&dev));
+    BK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // candidates: 1 .. bps co-resident CTAs per SM; timed on force evaluations, which
+    // run every phase but move no node
+    cudaEvent_t e0, e1;
+    BK(cudaEventCreate(&e0));
+    BK(cudaEventCreate(&e1));
+    BatchArgs a = b->args;
+    a.iters = 1;
+    a.advance = 0;
+    a.eval = 1;
+    float best = 1e30f;
+    int best_blocks = b->grid_blocks;
+    for (int c = 1; c <= bps; ++c) {
+        b->grid_blocks = c * sms;
+        BK(batch_launch(b, a, b->stream));  // warm-up
+        BK(cudaEventRecord(e0, b->stream));
+        for (int t = 0; t < trials; ++t) BK(batch_launch(b, a, b->stream));
+        BK(cudaEventRecord(e1, b->stream));
+        BK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        BK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_blocks = c * sms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->grid_blocks = best_blocks;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->exec_iters = -1;
+    if (chosen_blocks) *chosen_blocks = best_blocks;
+    return TFDP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+// fft_stages.cuh -- the three register-resident FFT stages of the grid interaction
+// (Sec. 3.4, second step) as device functions over one work item, shared by the
+// single-graph kernels (fft_kernels.cu) and the batched persistent kernel (batch.cu).
+//
+// The transforms evaluate the well-conditioned form of Eq. (Fr1)/(Fr2):
+//   A = K * rho,   O^x = (Delta_x K) * rho - K * m^x,   O^y likewise,
+// on a zero-padded P x P circulant (P >= 2G - 1): rows forward (real to half spectrum,
+// two real rows per complex transform), then per column forward / spectral product /
+// inverse, then rows inverse (half spectrum to real).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "fft_reg.cuh"
+
+namespace tfdp {
+
+// ---------------------------------------------------------------- row sources
+// Spread grid: gin[c][y][x] with row stride Gs and plane stride Gs * Gs; zero outside
+// the G x G grid of this iteration (the zero padding of the linear convolution).
+struct GridSource {
+    const float* gin;
+    int Gs;
+    __device__ __forceinline__ void bind(const DevState*, const DevParams*) {}
+    __device__ __forceinline__ int rows(const DevState* st) const { return st->grid.G; }
+    __device__ __forceinline__ bool active(const DevState* st) const { return true; }
+    __device__ __forceinline__ float operator()(int c, int y, int x, int G) const {
+        return (x < G && y < G) ? gin[((size_t)c * Gs + y) * Gs + x] : 0.0f;
+    }
+};
+
+// Kernel samples on the P x P circulant, wraparound offsets d -> d (d < P/2) or d - P.
+//   c = 0: K(D) = (1 + |D|^2 s^2)^-gamma,  c = 1: D_x s K(D),  c = 2: D_y s K(D),
+// with s = h / k the grid spacing. Entries with |D_x| = P/2 or |D_y| = P/2 are zero:
+// the cropped linear convolution never reads them, and zeroing keeps the odd
+// kernels exactly odd (their spectra exactly imaginary).
+struct KernelSource {
+    int P;
+    float s2, s, gamma;  // spacing^2, spacing, exponent (FP32)
+    int gamma_int;
+    __device__ __forceinline__ void bind(const DevState* st, const DevParams* prm) {
+        const double sd = st->grid.h / (double)prm->k;
+        s = (float)sd;
+        s2 = (float)(sd * sd);
+        gamma = (float)prm->gamma;
+        gamma_int = prm->gamma_int;
+    }
+    __device__ __forceinline__ int rows(const DevState*) const { return P; }
+    __device__ __forceinline__ bool active(const DevState* st) const { return st->spec_dirty != 0; }
+    __device__ __forceinline__ float operator()(int c, int y, int x, int) const {
+        const int half = P >> 1;
+        if (x == half || y == half) return 0.0f;
+        const int dx = (x < half) ? x : x - P;
+        const int dy = (y < half) ? y : y - P;
+        // dx^2 + dy^2 < 2^24 is exact in FP32
+        const float u = fmaf((float)(dx * dx + dy * dy), s2, 1.0f);
+        float K;
+        if (gamma_int > 0) {  // integer gamma: u^-gamma by multiplication
+            float ug = u;
+            for (int q = 1; q < gamma_int; ++q) ug *= u;
+            K = 1.0f / ug;
+        } else {
+            K = powf(u, -gamma);
+        }
+        if (c == 0) return K;
+        return (float)(c == 1 ? dx : dy) * s * K;
+    }
+};
+
+// ---------------------------------------------------------------- register-resident path
+// Same transforms as k_rows_fwd / k_cols / k_rows_inv, with each thread holding eight
+// values of each of its three sequences (fft_reg.cuh). RG row pairs (or columns) per
+// CTA, T = P/8 threads each.
+template <int LOGP>
+struct RegGeom {
+    static constexpr int P = 1 << LOGP;
+    static constexpr int T = P / 8;
+    static constexpr int RG = (T >= 256) ? 1 : 256 / T;   // row pairs per CTA (rows kernels), <= 16
+    static constexpr int CG = (T >= 256) ? 1 : 256 / T;   // columns per CTA (column kernel)
+    static constexpr size_t rows_smem = (size_t)RG * 3 * P * sizeof(float2);
+    static constexpr size_t cols_smem = (size_t)CG * 3 * P * sizeof(float2);
+};
+
+// Forward row transforms of row block `blk` (2 RG rows x 3 channels) of a source into
+// out[c][kx][ystride] (half spectrum along x, column-major).
+template <int LOGP, class Src>
+__device__ __forceinline__ void rows_fwd_body(const Src& src, int nrows, int blk, float2* __restrict__ out,
+                                              int ystride, const float2* __restrict__ tw, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    const int G = nrows;
+    const int ybase = blk * (2 * RG);
+    if (ybase >= G) return;
+    const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
+    const int y0 = ybase + 2 * lr;
+    float2* smr = sm + (size_t)lr * 3 * P;
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int x = t + r * T;
+            v[c][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+        }
+    reg_fft_forward<LOGP, 3>(v, smr, tw, t);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) smr[c * P + swz(8 * t + r)] = v[c][r];
+    __syncthreads();
+    // split Z = FFT(a + i b) into FFT(a), FFT(b); one thread per (channel, kx) writes
+    // 2 RG consecutive rows (RG row pairs) of out[c][kx][.]
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = idx - c * NH;
+        const int pk = swz(pos_of_freq<LOGP>(kx));
+        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+        float4* dst = reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + ybase);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float2* seq = sm + ((size_t)q * 3 + c) * P;
+            const float2 Z = seq[pk], W = seq[pn];
+            dst[q] = make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+        }
+    }
+}
+
+// Column block cblk (CG columns kx): forward along y of (rho, m^x, m^y) from T1,
+// spectral product A = K rho, O^x = i hx rho - K m^x, O^y = i hy rho - K m^y, inverse along
+// y, rows y < G to T2. When spec_dirty, the kernel spectra of these columns are first
+// rebuilt from the row-transformed kernel samples in S1 (and stored).
+template <int LOGP>
+__device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T1, float2* __restrict__ T2,
+                                          int ystride, float* __restrict__ specK, float* __restrict__ specHx,
+                                          float* __restrict__ specHy, const float2* __restrict__ S1,
+                                          const float2* __restrict__ tw, int G, int spec_dirty, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
+    const int lc = threadIdx.x / T, t = threadIdx.x - lc * T;
+    const int kx = cblk * Gm::CG + lc;
+    const bool valid = kx < NH;
+    float2* smc = sm + (size_t)lc * 3 * P;
+    float2 v[3][8];
+    // kernel spectra at this thread's output positions 8t .. 8t+7 (digit-reversed order)
+    float K[8], hx[8], hy[8];
+    const size_t so = (size_t)(valid ? kx : 0) * P + 8 * t;
+    if (spec_dirty) {
+        // rebuild: forward transform along y of the row-transformed kernel samples
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+                v[c][r] = valid ? S1[((size_t)c * NH + kx) * P + t + r * T] : make_float2(0.f, 0.f);
+        reg_fft_forward<LOGP, 3>(v, smc, tw, t);
+        const float inv = 1.0f / ((float)P * (float)P);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            K[r] = v[0][r].x * inv;
+            hx[r] = v[1][r].y * inv;
+            hy[r] = v[2][r].y * inv;
+        }
+        if (valid) {
+            float4* pK = reinterpret_cast<float4*>(specK + so);
+            float4* pX = reinterpret_cast<float4*>(specHx + so);
+            float4* pY = reinterpret_cast<float4*>(specHy + so);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                pK[h] = make_float4(K[4 * h], K[4 * h + 1], K[4 * h + 2], K[4 * h + 3]);
+                pX[h] = make_float4(hx[4 * h], hx[4 * h + 1], hx[4 * h + 2], hx[4 * h + 3]);
+                pY[h] = make_float4(hy[4 * h], hy[4 * h + 1], hy[4 * h + 2], hy[4 * h + 3]);
+            }
+        }
+        __syncthreads();  // shared memory is reused by the data transform
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = t + r * T;
+            v[c][r] = (valid && y < G) ? T1[((size_t)c * NH + kx) * ystride + y] : make_float2(0.f, 0.f);
+        }
+    reg_fft_forward<LOGP, 3>(v, smc, tw, t);
+    if (valid) {
+        // spectra at the output positions; loaded here (not before the transform) to keep
+        // them out of the registers the transform needs; after a rebuild this re-reads
+        // what this thread just wrote
+        const float4* pK = reinterpret_cast<const float4*>(specK + so);
+        const float4* pX = reinterpret_cast<const float4*>(specHx + so);
+        const float4* pY = reinterpret_cast<const float4*>(specHy + so);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float4 a = pK[h], b = pX[h], d = pY[h];
+            K[4 * h] = a.x; K[4 * h + 1] = a.y; K[4 * h + 2] = a.z; K[4 * h + 3] = a.w;
+            hx[4 * h] = b.x; hx[4 * h + 1] = b.y; hx[4 * h + 2] = b.z; hx[4 * h + 3] = b.w;
+            hy[4 * h] = d.x; hy[4 * h + 1] = d.y; hy[4 * h + 2] = d.z; hy[4 * h + 3] = d.w;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float2 rr = v[0][r], mx = v[1][r], my = v[2][r];
+            v[0][r] = make_float2(K[r] * rr.x, K[r] * rr.y);
+            v[1][r] = make_float2(-hx[r] * rr.y - K[r] * mx.x, hx[r] * rr.x - K[r] * mx.y);
+            v[2][r] = make_float2(-hy[r] * rr.y - K[r] * my.x, hy[r] * rr.x - K[r] * my.y);
+        }
+    }
+    reg_fft_inverse<LOGP, 3>(v, smc, tw, t);
+    if (valid) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const int y = t + r * T;
+                if (y < G) T2[((size_t)c * NH + kx) * ystride + y] = v[c][r];
+            }
+    }
+}
+
+// Row block blk (RG row pairs): complex-to-real along x of the three outputs from T2,
+// two real rows per complex transform, written as (A, O^x, O^y, 0) for x, y < G.
+template <int LOGP>
+__device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict__ T2, int ystride,
+                                              float4* __restrict__ gout, int Gs, const float2* __restrict__ tw,
+                                              int G, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    const int ybase = blk * (2 * RG);
+    if (ybase >= G) return;
+    // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = idx - c * NH;
+        const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
+        const int pk = swz(pos_of_freq<LOGP>(kx));
+        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const int y = ybase + 2 * q;
+            float4 X = (y < G) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (y + 1 >= G) { X.z = 0.f; X.w = 0.f; }  // row past G: never written
+            float2* seq = sm + ((size_t)q * 3 + c) * P;
+            seq[pk] = make_float2(X.x - X.w, X.y + X.z);
+            if (kx != 0 && kx != P / 2) seq[pn] = make_float2(X.x + X.w, X.z - X.y);
+        }
+    }
+    __syncthreads();
+    const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
+    const int y0 = ybase + 2 * lr;
+    float2* smr = sm + (size_t)lr * 3 * P;
+    float2 v[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[c][r] = smr[c * P + swz(8 * t + r)];
+    reg_fft_inverse<LOGP, 3>(v, smr, tw, t);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int x = t + r * T;
+        if (x >= G) continue;
+        if (y0 < G) gout[(size_t)y0 * Gs + x] = make_float4(v[0][r].x, v[1][r].x, v[2][r].x, 0.0f);
+        if (y0 + 1 < G) gout[(size_t)(y0 + 1) * Gs + x] = make_float4(v[0][r].y, v[1][r].y, v[2][r].y, 0.0f);
+    }
+}
+
+}  // namespace tfdp

@@ -1,0 +1,220 @@
+// node_dev.cuh -- per-node device functions of the ibFFT path and the update, shared
+// by the single-graph kernels (node_kernels.cu) and the batched persistent kernel
+// (batch.cu) so that both compute identical per-node arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "common.cuh"
+
+namespace tfdp {
+
+// ---------------------------------------------------------------- box geometry
+struct AxisGeom {
+    float lo, h_hi, h_lo, hk;  // origin, box side as hi + lo FP32 pair, h / k
+    int n_int;
+};
+
+__device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g) {
+    AxisGeom a;
+    a.lo = g.lo_f;
+    a.h_hi = g.h_f;
+    a.h_lo = g.h_lo_f;
+    a.hk = g.hk_f;
+    a.n_int = g.n_int;
+    return a;
+}
+
+// Box index b (the FP32 decision shared with the oracle) and the offset of x from the
+// box origin lo + b h, accurate to a few ulps of h.
+__device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off) {
+    float tq;
+    const int b = box_of(x, a.lo, a.h_hi, a.n_int, &tq);
+    // x - lo = s + e exactly (TwoSum)
+    const float s = __fsub_rn(x, a.lo);
+    const float bb = __fsub_rn(s, x);
+    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-a.lo, bb));
+    // b * h_hi = p + pe exactly
+    const float fb = (float)b;
+    const float p = __fmul_rn(fb, a.h_hi);
+    const float pe = __fmaf_rn(fb, a.h_hi, -p);
+    *off = __fadd_rn(__fsub_rn(s, p), __fsub_rn(__fsub_rn(e, pe), __fmul_rn(fb, a.h_lo)));
+    return b;
+}
+
+__device__ __forceinline__ float warp_sumf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- attraction + update
+// alpha * sum_{j <-> i} (1 + beta / (1 + d^2)) (x_j - x_i), Eq. (newforce).
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col, const float2* __restrict__ xy,
+                                             float alpha, float beta) {
+    float fx = 0.0f, fy = 0.0f;
+    int e = rowptr[i];
+    const int e1 = rowptr[i + 1];
+    // four neighbours per round so that their loads are in flight together
+    for (; e + 4 <= e1; e += 4) {
+        int j[4];
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float dx = q[u].x - p.x, dy = q[u].y - p.y;
+            const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            fx = fmaf(c, dx, fx);
+            fy = fmaf(c, dy, fy);
+        }
+    }
+    for (; e < e1; ++e) {
+        const float2 q = xy[__ldg(col + e)];
+        const float dx = q.x - p.x, dy = q.y - p.y;
+        const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+        fx = fmaf(c, dx, fx);
+        fy = fmaf(c, dy, fy);
+    }
+    return make_float2(alpha * fx, alpha * fy);
+}
+
+// x + D min(1, s / |D|)
+__device__ __forceinline__ float2 capped_step(float2 p, float2 D, float s) {
+    const float d2 = D.x * D.x + D.y * D.y;
+    const float c = (d2 > s * s) ? s * rsqrtf(d2) : 1.0f;
+    return make_float2(fmaf(c, D.x, p.x), fmaf(c, D.y, p.y));
+}
+
+// The grid of iteration t = st->iter from the layout extremes (exact FP64 decisions),
+// the step s_t, the spectrum key and the bookkeeping of the iteration (one thread).
+__device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, int advance) {
+    const long long t = st->iter;
+    const int cur = (int)(t & 1);
+    const GridDesc g = make_grid(ord2f(st->bbox[cur][0]), ord2f(st->bbox[cur][1]), prm);
+    st->grid = g;
+    st->t_cur = t;
+    st->step_cur = step_size(t, prm);
+    st->net_frep[0] = 0.0;
+    st->net_frep[1] = 0.0;
+    if (advance) {
+        st->bbox[cur ^ 1][0] = kOrdMinInit;
+        st->bbox[cur ^ 1][1] = kOrdMaxInit;
+    }
+    const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
+                       st->spec_k == prm.k && st->spec_P == prm.P;
+    st->spec_dirty = valid ? 0 : 1;
+    if (!valid) {
+        st->spec_h = g.h;
+        st->spec_gamma = prm.gamma;
+        st->spec_k = prm.k;
+        st->spec_P = prm.P;
+        st->spec_valid = 1;
+        st->spec_builds += 1;
+    }
+}
+
+// ---------------------------------------------------------------- spread and gather
+// Fixed-point scale of the spread sums. Each term w (|w| <= 3.52 for k <= 3, since a
+// 1D Lagrange weight on [0, 1) is at most 1.875) and w d / h (|d| <= 1.5 h) is rounded
+// to an int32 multiple of 2^-27 and summed in int64: the sums are exact, so they do not
+// depend on the order of the nodes in a box (which the parallel sort leaves open) and
+// every iteration is bitwise reproducible. The quantum 2^-27 = 7.5e-9 is far below the
+// FP32 resolution of the results.
+constexpr float kSpreadScale = 134217728.0f;       // 2^27
+constexpr float kSpreadInvScale = 1.0f / 134217728.0f;
+
+__device__ __forceinline__ long long spread_q(float v) {
+    // round to nearest; NaN -> 0 and saturation keep the conversion defined
+    const float s = fminf(fmaxf(v * kSpreadScale, -2.0e9f), 2.0e9f);
+    return (long long)__float2int_rn(s);
+}
+
+// Lagrange projection (Sec. 3.4 step 1) of the nodes sxy[s0, s1) of box (bx, by) onto its
+// K x K grid nodes: rho = sum w, m^x = sum w (x - y^x), m^y = sum w (y - y^y), written to
+// the three planes of gin (row stride Gs, plane stride Gs^2).
+template <int K>
+__device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s0, int s1, int bx, int by,
+                                           const AxisGeom& ag, float* __restrict__ gin, int Gs) {
+    const size_t plane = (size_t)Gs * Gs;
+    long long rho[K][K], mx[K][K], my[K][K];  // fixed point; moments in units of h
+#pragma unroll
+    for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+        for (int lx = 0; lx < K; ++lx) rho[ly][lx] = mx[ly][lx] = my[ly][lx] = 0;
+    const float inv_h = 1.0f / ag.h_hi;
+    for (int s = s0; s < s1; ++s) {
+        const float2 p = sxy[s];
+        float ox, oy;
+        box_offset(p.x, ag, &ox);
+        box_offset(p.y, ag, &oy);
+        float wx[K], wy[K], dx[K], dy[K];
+        lagrange<K>(ox / ag.h_hi, wx);
+        lagrange<K>(oy / ag.h_hi, wy);
+#pragma unroll
+        for (int l = 0; l < K; ++l) {
+            dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
+            dy[l] = (oy - ((float)l + 0.5f) * ag.hk) * inv_h;
+        }
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) {
+                const float w = wx[lx] * wy[ly];
+                rho[ly][lx] += spread_q(w);
+                mx[ly][lx] += spread_q(w * dx[lx]);
+                my[ly][lx] += spread_q(w * dy[ly]);
+            }
+    }
+    const float hs = ag.h_hi * kSpreadInvScale;
+#pragma unroll
+    for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+        for (int lx = 0; lx < K; ++lx) {
+            const size_t q = (size_t)(by * K + ly) * Gs + (bx * K + lx);
+            gin[q] = (float)rho[ly][lx] * kSpreadInvScale;
+            gin[plane + q] = (float)mx[ly][lx] * hs;
+            gin[2 * plane + q] = (float)my[ly][lx] * hs;
+        }
+}
+
+// Back-projection (Sec. 3.4 step 3) at position p from the grid (A, O^x, O^y, 0):
+// frep = sum_q w_q [ (p - y_q) A_q + O_q ], the well-conditioned Eq. (Fr1)/(Fr2).
+template <int K>
+__device__ __forceinline__ float2 gather_frep(float2 p, const AxisGeom& ag, const float4* __restrict__ gout, int Gs) {
+    float ox, oy;
+    const int bx = box_offset(p.x, ag, &ox);
+    const int by = box_offset(p.y, ag, &oy);
+    float wx[K], wy[K], dx[K], dy[K];
+    lagrange<K>(ox / ag.h_hi, wx);
+    lagrange<K>(oy / ag.h_hi, wy);
+#pragma unroll
+    for (int l = 0; l < K; ++l) {
+        dx[l] = ox - ((float)l + 0.5f) * ag.hk;
+        dy[l] = oy - ((float)l + 0.5f) * ag.hk;
+    }
+    float frx = 0.0f, fry = 0.0f;
+#pragma unroll
+    for (int ly = 0; ly < K; ++ly) {
+        const float4* row = gout + (size_t)(by * K + ly) * Gs + bx * K;
+#pragma unroll
+        for (int lx = 0; lx < K; ++lx) {
+            const float4 v = __ldg(row + lx);  // (A, O^x, O^y, 0)
+            const float w = wx[lx] * wy[ly];
+            frx = fmaf(w, fmaf(dx[lx], v.x, v.y), frx);
+            fry = fmaf(w, fmaf(dy[ly], v.x, v.z), fry);
+        }
+    }
+    return make_float2(frx, fry);
+}
+
+}  // namespace tfdp

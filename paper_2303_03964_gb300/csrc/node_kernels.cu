@@ -21,6 +21,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "node_dev.cuh"
 
 namespace tfdp {
 
@@ -31,49 +32,12 @@ constexpr int kNodeThreads = 256;
 
 int scan_items_per_block() { return kScanChunk; }
 
-// ---------------------------------------------------------------- box geometry
-struct AxisGeom {
-    float lo, h_hi, h_lo, hk;  // origin, box side as hi + lo FP32 pair, h / k
-    int n_int;
-};
-
-__device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g) {
-    AxisGeom a;
-    a.lo = g.lo_f;
-    a.h_hi = g.h_f;
-    a.h_lo = g.h_lo_f;
-    a.hk = g.hk_f;
-    a.n_int = g.n_int;
-    return a;
-}
-
-// Box index b (the FP32 decision shared with the oracle) and the offset of x from the
-// box origin lo + b h, accurate to a few ulps of h.
-__device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off) {
-    float tq;
-    const int b = box_of(x, a.lo, a.h_hi, a.n_int, &tq);
-    // x - lo = s + e exactly (TwoSum)
-    const float s = __fsub_rn(x, a.lo);
-    const float bb = __fsub_rn(s, x);
-    const float e = __fadd_rn(__fsub_rn(x, __fsub_rn(s, bb)), __fsub_rn(-a.lo, bb));
-    // b * h_hi = p + pe exactly
-    const float fb = (float)b;
-    const float p = __fmul_rn(fb, a.h_hi);
-    const float pe = __fmaf_rn(fb, a.h_hi, -p);
-    *off = __fadd_rn(__fsub_rn(s, p), __fsub_rn(__fsub_rn(e, pe), __fmul_rn(fb, a.h_lo)));
-    return b;
-}
-
 // ---------------------------------------------------------------- reductions
 struct BlockAcc {
     float mn, mx;
     double fx, fy;
 };
 
-__device__ __forceinline__ float warp_sumf(float v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Reduce (min, max, sum fx, sum fy) over the block; thread 0 publishes with atomics.
 // The force sums are FP32 within a warp (one node per thread) and FP64 above.
@@ -136,83 +100,12 @@ __global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict_
     }
 }
 
-// ---------------------------------------------------------------- attraction + update
-// alpha * sum_{j <-> i} (1 + beta / (1 + d^2)) (x_j - x_i), Eq. (newforce).
-__device__ __forceinline__ float rcp_fast(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
-                                             const int* __restrict__ col, const float2* __restrict__ xy,
-                                             float alpha, float beta) {
-    float fx = 0.0f, fy = 0.0f;
-    int e = rowptr[i];
-    const int e1 = rowptr[i + 1];
-    // four neighbours per round so that their loads are in flight together
-    for (; e + 4 <= e1; e += 4) {
-        int j[4];
-        float2 q[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + u);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float dx = q[u].x - p.x, dy = q[u].y - p.y;
-            const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
-            fx = fmaf(c, dx, fx);
-            fy = fmaf(c, dy, fy);
-        }
-    }
-    for (; e < e1; ++e) {
-        const float2 q = xy[__ldg(col + e)];
-        const float dx = q.x - p.x, dy = q.y - p.y;
-        const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
-        fx = fmaf(c, dx, fx);
-        fy = fmaf(c, dy, fy);
-    }
-    return make_float2(alpha * fx, alpha * fy);
-}
-
-// x + D min(1, s / |D|)
-__device__ __forceinline__ float2 capped_step(float2 p, float2 D, float s) {
-    const float d2 = D.x * D.x + D.y * D.y;
-    const float c = (d2 > s * s) ? s * rsqrtf(d2) : 1.0f;
-    return make_float2(fmaf(c, D.x, p.x), fmaf(c, D.y, p.y));
-}
-
 // ---------------------------------------------------------------- FFT path: grid
 // One thread: the grid of this iteration from the layout extremes (exact FP64
 // decisions), the step s_t, the spectrum key, and the bookkeeping of the iteration.
 __global__ void k_grid(NodeLaunch a, int advance) {
     if (threadIdx.x != 0) return;
-    DevState* st = a.st;
-    const DevParams prm = *a.prm;
-    const long long t = st->iter;
-    const int cur = (int)(t & 1);
-    const GridDesc g = make_grid(ord2f(st->bbox[cur][0]), ord2f(st->bbox[cur][1]), prm);
-    st->grid = g;
-    st->t_cur = t;
-    st->step_cur = step_size(t, prm);
-    st->net_frep[0] = 0.0;
-    st->net_frep[1] = 0.0;
-    if (advance) {
-        st->bbox[cur ^ 1][0] = kOrdMinInit;
-        st->bbox[cur ^ 1][1] = kOrdMaxInit;
-    }
-    const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
-                       st->spec_k == prm.k && st->spec_P == prm.P;
-    st->spec_dirty = valid ? 0 : 1;
-    if (!valid) {
-        st->spec_h = g.h;
-        st->spec_gamma = prm.gamma;
-        st->spec_k = prm.k;
-        st->spec_P = prm.P;
-        st->spec_valid = 1;
-        st->spec_builds += 1;
-    }
+    grid_decide(a.st, *a.prm, advance);
 }
 
 // Box of every node (the FP32 decision) and its slot in the box (counting-sort
@@ -400,50 +293,11 @@ __global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
     const GridDesc g = a.st->grid;
     const int nbox = g.n_int * g.n_int;
     const AxisGeom ag = axis_geom(g);
-    const size_t plane = (size_t)a.Gs * a.Gs;
     const float2* __restrict__ sxy = a.vxy[(int)(a.st->t_cur & 1) ^ 1];
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
         const int by = b / g.n_int;
         const int bx = b - by * g.n_int;
-        float rho[K][K], mx[K][K], my[K][K];
-#pragma unroll
-        for (int ly = 0; ly < K; ++ly)
-#pragma unroll
-            for (int lx = 0; lx < K; ++lx) rho[ly][lx] = mx[ly][lx] = my[ly][lx] = 0.0f;
-        const int s0 = max(a.off[b], 0);
-        const int s1 = min(a.off[b + 1], a.n);
-        for (int s = s0; s < s1; ++s) {
-            const float2 p = sxy[s];
-            float ox, oy;
-            box_offset(p.x, ag, &ox);
-            box_offset(p.y, ag, &oy);
-            float wx[K], wy[K], dx[K], dy[K];
-            lagrange<K>(ox / ag.h_hi, wx);
-            lagrange<K>(oy / ag.h_hi, wy);
-#pragma unroll
-            for (int l = 0; l < K; ++l) {
-                dx[l] = ox - ((float)l + 0.5f) * ag.hk;
-                dy[l] = oy - ((float)l + 0.5f) * ag.hk;
-            }
-#pragma unroll
-            for (int ly = 0; ly < K; ++ly)
-#pragma unroll
-                for (int lx = 0; lx < K; ++lx) {
-                    const float w = wx[lx] * wy[ly];
-                    rho[ly][lx] += w;
-                    mx[ly][lx] = fmaf(w, dx[lx], mx[ly][lx]);
-                    my[ly][lx] = fmaf(w, dy[ly], my[ly][lx]);
-                }
-        }
-#pragma unroll
-        for (int ly = 0; ly < K; ++ly)
-#pragma unroll
-            for (int lx = 0; lx < K; ++lx) {
-                const size_t q = (size_t)(by * K + ly) * a.Gs + (bx * K + lx);
-                a.gin[q] = rho[ly][lx];
-                a.gin[plane + q] = mx[ly][lx];
-                a.gin[2 * plane + q] = my[ly][lx];
-            }
+        spread_box<K>(sxy, max(a.off[b], 0), min(a.off[b + 1], a.n), bx, by, ag, a.gin, a.Gs);
     }
 }
 
@@ -491,29 +345,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a, in
         const int i = perm[s];
         if ((unsigned)i >= (unsigned)a.n) continue;  // only after a failed sort (flagged there)
         const float2 fa = a.fatt_out[i];
-        float ox, oy;
-        const int bx = box_offset(p.x, ag, &ox);
-        const int by = box_offset(p.y, ag, &oy);
-        float wx[K], wy[K], dx[K], dy[K];
-        lagrange<K>(ox / ag.h_hi, wx);
-        lagrange<K>(oy / ag.h_hi, wy);
-#pragma unroll
-        for (int l = 0; l < K; ++l) {
-            dx[l] = ox - ((float)l + 0.5f) * ag.hk;
-            dy[l] = oy - ((float)l + 0.5f) * ag.hk;
-        }
-        float frx = 0.0f, fry = 0.0f;
-#pragma unroll
-        for (int ly = 0; ly < K; ++ly) {
-            const float4* row = a.gout + (size_t)(by * K + ly) * a.Gs + bx * K;
-#pragma unroll
-            for (int lx = 0; lx < K; ++lx) {
-                const float4 v = __ldg(row + lx);  // (A, O^x, O^y, 0)
-                const float w = wx[lx] * wy[ly];
-                frx = fmaf(w, fmaf(dx[lx], v.x, v.y), frx);
-                fry = fmaf(w, fmaf(dy[ly], v.x, v.z), fry);
-            }
-        }
+        const float2 fg = gather_frep<K>(p, ag, a.gout, a.Gs);
+        const float frx = fg.x, fry = fg.y;
         sfx += frx;
         sfy += fry;
         if (EVAL) {

@@ -784,6 +784,39 @@ tfdp_status tfdp_synchronize(tfdp_graph* g) {
     return TFDP_OK;
 }
 
+tfdp_status tfdp_graph_set_stream(tfdp_graph* g, void* stream) {
+    if (!g) return TFDP_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(g->stream));  // work queued on the old stream completes first
+    g->stream = (cudaStream_t)stream;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params, size_t* bytes) {
+    if (!bytes || n < 0 || m < 0) return TFDP_ERR_INVALID_ARG;
+    tfdp_params p;
+    if (params) p = *params;
+    else tfdp_params_default(&p);
+    tfdp_status st = tfdp_params_check(&p, nullptr);
+    if (st != TFDP_OK) return st;
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
+    const int nchunks = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+    size_t b = 0;
+    b += sizeof(float2) * nn * (4 + (size_t)nchunks) + sizeof(int) * (nn + 1) + sizeof(int) * (size_t)(2 * m);
+    b += sizeof(DevParams) + sizeof(DevState) + sizeof(double) * (size_t)p.total_iters + 16 * 256;
+    if (p.rep_mode == TFDP_REP_FFT) {
+        int P, logP, G_max, nbox_max;
+        if (!fft_geometry(p, &P, &logP, &G_max, &nbox_max)) return TFDP_ERR_PARAM_RANGE;
+        const size_t Gs = align_up((size_t)G_max, 4), ys = align_up((size_t)G_max, 32), NH = (size_t)P / 2 + 1;
+        b += sizeof(int) * (align_up((size_t)nbox_max, 8192) + nbox_max + 1) + 8 * 1024;
+        b += nn * (sizeof(int2) + 2 * sizeof(int) + 2 * sizeof(float2) + sizeof(int));
+        b += sizeof(float) * 3 * Gs * Gs + 2 * sizeof(float2) * 3 * NH * ys + sizeof(float4) * Gs * Gs;
+        b += sizeof(float2) * 3 * NH * P + 3 * sizeof(float) * NH * P + sizeof(float2) * P + 32 * 256;
+    }
+    *bytes = b;
+    return TFDP_OK;
+}
+
 tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
     if (!g) return TFDP_OK;
     if (g->stream || g->cap_stream) cudaStreamSynchronize(g->stream);

@@ -173,3 +173,27 @@ def ba_2m(rng=None, n=2_000_000, m0=3):
     e = barabasi_albert(n, m0, rng)
     xy = uniform_positions(n, np.sqrt(n) / 2.0, rng)
     return e, xy
+
+
+def batch_mixed(count=512, nmin=1000, nmax=50000, rng=None):
+    """`count` graphs with n log-uniform in [nmin, nmax]; in turn an SBM (10 blocks, mean
+    degree 8, 90% inside blocks), a Barabasi-Albert graph (m0 = 2) and a lattice
+    (side floor(sqrt n)); positions uniform with unit density. Returns a list of
+    (n, edges, xy)."""
+    rng = rng or rng_for(4)
+    out = []
+    for q in range(count):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        kind = q % 3
+        if kind == 0:
+            n = max(10, n // 10 * 10)
+            e, _ = sbm(n, 10, 8.0, 0.9, rng)
+        elif kind == 1:
+            e = barabasi_albert(n, 2, rng)
+        else:
+            side = max(2, int(np.sqrt(n)))
+            n = side * side
+            e = lattice(side, side)
+        xy = uniform_positions(n, np.sqrt(n) / 2.0, rng)
+        out.append((n, e, xy))
+    return out

@@ -80,6 +80,26 @@ _SIGS = {
     "tfdp_destroy_graph": ([_p], ctypes.c_int),
     "tfdp_debug_fetch": ([_p, ctypes.c_int, _p, ctypes.c_size_t], ctypes.c_int),
     "tfdp_exact_repulsion_noalloc": ([_p, ctypes.c_int64, ctypes.c_double, _p, _p], ctypes.c_int),
+    "tfdp_batch_create": ([ctypes.c_int32, _p, _p, _p, _p, _p, _p, ctypes.POINTER(_p)], ctypes.c_int),
+    "tfdp_batch_iterate": ([_p, ctypes.c_int32], ctypes.c_int),
+    "tfdp_batch_eval_forces": ([_p, ctypes.c_int32, _p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_batch_get_positions": ([_p, ctypes.c_int32, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_batch_get_stats": ([_p, ctypes.c_int32, ctypes.POINTER(Stats)], ctypes.c_int),
+    "tfdp_batch_synchronize": ([_p], ctypes.c_int),
+    "tfdp_batch_destroy": ([_p], ctypes.c_int),
+    "tfdp_batch_grid_blocks": ([_p], ctypes.c_int32),
+    "tfdp_batch_autotune": ([_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "tfdp_graph_set_stream": ([_p, _p], ctypes.c_int),
+    "tfdp_graph_footprint": ([ctypes.c_int64, ctypes.c_int64, _p, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "tfdp_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_p)], ctypes.c_int),
+    "tfdp_server_submit": ([_p, ctypes.c_int64, ctypes.c_int64, _p, _p, _p, ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "tfdp_server_update": ([_p, ctypes.c_int64, _p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "tfdp_server_poll": ([_p, _p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32], ctypes.c_int),
+    "tfdp_server_get_positions": ([_p, ctypes.c_int64, _p], ctypes.c_int),
+    "tfdp_server_release": ([_p, ctypes.c_int64], ctypes.c_int),
+    "tfdp_server_get_stats": ([_p, _p], ctypes.c_int),
+    "tfdp_server_destroy": ([_p], ctypes.c_int),
 }
 
 NOALLOC_MAX_N = 16384
@@ -266,3 +286,164 @@ def exact_repulsion_noalloc(xy, frep, gamma=2.0, stream=0):
                                             _p(frep.data_ptr()), _p(stream or 0)),
            "tfdp_exact_repulsion_noalloc")
     return frep
+
+
+class Batch:
+    """Many graphs advanced together by one persistent launch (wraps tfdp_batch).
+
+    ``graphs`` is a list of (n, edges (m x 2 int32), xy0 (n x 2 float32)); ``params`` is
+    None (defaults) or one Params per graph (all with the same k_interp).
+    """
+
+    def __init__(self, graphs, params=None, stream=0):
+        B = len(graphs)
+        self.B = B
+        self._n = np.array([int(g[0]) for g in graphs], dtype=np.int64)
+        self._edges = [np.ascontiguousarray(np.asarray(g[1], dtype=np.int32).reshape(-1, 2)) for g in graphs]
+        self._xy = [_host_f32(g[2], int(g[0])) for g in graphs]
+        m = np.array([e.shape[0] for e in self._edges], dtype=np.int64)
+        eptr = (_p * B)(*[e.ctypes.data if e.shape[0] else None for e in self._edges])
+        xptr = (_p * B)(*[x.ctypes.data for x in self._xy])
+        prm = None
+        if params is not None:
+            prm = (Params * B)()
+            for i, p in enumerate(params):
+                ctypes.memmove(ctypes.byref(prm[i]), ctypes.byref(p), ctypes.sizeof(Params))
+        h = _p()
+        _check(lib.tfdp_batch_create(B, self._n.ctypes.data_as(_p), m.ctypes.data_as(_p),
+                                     ctypes.cast(eptr, _p), ctypes.cast(xptr, _p),
+                                     ctypes.cast(prm, _p) if prm is not None else None,
+                                     _p(stream or 0), ctypes.byref(h)), "tfdp_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.tfdp_batch_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def iterate(self, iters=1):
+        _check(lib.tfdp_batch_iterate(self._h, int(iters)), "tfdp_batch_iterate")
+
+    def synchronize(self):
+        _check(lib.tfdp_batch_synchronize(self._h), "tfdp_batch_synchronize")
+
+    def eval_forces(self, g):
+        n = int(self._n[g])
+        fr = np.empty((n, 2), dtype=np.float32)
+        fa = np.empty((n, 2), dtype=np.float32)
+        _check(lib.tfdp_batch_eval_forces(self._h, int(g), fr.ctypes.data_as(_p), fa.ctypes.data_as(_p), 0),
+               "tfdp_batch_eval_forces")
+        return fr, fa
+
+    def get_positions(self, g):
+        a = np.empty((int(self._n[g]), 2), dtype=np.float32)
+        _check(lib.tfdp_batch_get_positions(self._h, int(g), a.ctypes.data_as(_p), 0), "tfdp_batch_get_positions")
+        return a
+
+    def stats(self, g):
+        s = Stats()
+        _check(lib.tfdp_batch_get_stats(self._h, int(g), ctypes.byref(s)), "tfdp_batch_get_stats")
+        return s.as_dict()
+
+    def grid_blocks(self):
+        return int(lib.tfdp_batch_grid_blocks(self._h))
+
+    def autotune(self, trials=3):
+        c = ctypes.c_int32(0)
+        _check(lib.tfdp_batch_autotune(self._h, int(trials), ctypes.byref(c)), "tfdp_batch_autotune")
+        return int(c.value)
+
+
+def graph_footprint(n, m, params=None):
+    """Device bytes a graph of n nodes and m edges would take."""
+    out = ctypes.c_size_t(0)
+    _check(lib.tfdp_graph_footprint(int(n), int(m), ctypes.byref(params) if params is not None else None,
+                                    ctypes.byref(out)), "tfdp_graph_footprint")
+    return int(out.value)
+
+
+class Done(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_int64), ("job_id", ctypes.c_int64), ("kind", ctypes.c_int32),
+                ("iters", ctypes.c_int32), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("active", ctypes.c_int32), ("peak_active", ctypes.c_int32), ("waiting", ctypes.c_int32),
+                ("jobs", ctypes.c_int32), ("used_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("node_iterations", ctypes.c_int64), ("reserved", ctypes.c_int32 * 8)]
+
+
+class Server:
+    """Interactive layout serving with continuous batching (wraps tfdp_server)."""
+
+    def __init__(self, budget_bytes, max_active=8, chunk_iters=10):
+        h = _p()
+        _check(lib.tfdp_server_create(int(budget_bytes), int(max_active), int(chunk_iters), ctypes.byref(h)),
+               "tfdp_server_create")
+        self._h = h
+        self._n = {}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib.tfdp_server_destroy(self._h)
+            self._h = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, n, edges, xy0, params=None, iters=300):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        x = _host_f32(xy0, n)
+        job, req = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(lib.tfdp_server_submit(self._h, int(n), e.shape[0], e.ctypes.data_as(_p) if e.shape[0] else None,
+                                      x.ctypes.data_as(_p), ctypes.byref(params) if params is not None else None,
+                                      int(iters), ctypes.byref(job), ctypes.byref(req)), "tfdp_server_submit")
+        self._n[job.value] = int(n)
+        return job.value, req.value
+
+    def update(self, job, params, iters=50):
+        req = ctypes.c_int64(0)
+        _check(lib.tfdp_server_update(self._h, int(job), ctypes.byref(params), int(iters), ctypes.byref(req)),
+               "tfdp_server_update")
+        return req.value
+
+    def poll(self, max_items=256, wait_ms=0):
+        buf = (Done * max_items)()
+        c = ctypes.c_int32(0)
+        _check(lib.tfdp_server_poll(self._h, buf, int(max_items), ctypes.byref(c), int(wait_ms)), "tfdp_server_poll")
+        return [{f: getattr(buf[i], f) for f, _ in Done._fields_ if f != "reserved"} for i in range(c.value)]
+
+    def positions(self, job):
+        a = np.empty((self._n[job], 2), dtype=np.float32)
+        _check(lib.tfdp_server_get_positions(self._h, int(job), a.ctypes.data_as(_p)), "tfdp_server_get_positions")
+        return a
+
+    def release(self, job):
+        _check(lib.tfdp_server_release(self._h, int(job)), "tfdp_server_release")
+
+    def stats(self):
+        s = ServerStats()
+        _check(lib.tfdp_server_get_stats(self._h, ctypes.byref(s)), "tfdp_server_get_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_ if f != "reserved"}

@@ -1,0 +1,91 @@
+"""Batched persistent launch: every graph of a batch must give the forces and the
+short layout of its solo run (and, through it, of the oracle)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_03964_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-5
+POS_TOL = 1e-4
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _mixed_graphs(count, seed, nmin=300, nmax=6000):
+    """Log-uniform sizes; SBM (10 blocks, mean degree 8), BA (m0 = 2) and lattices in turn."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        n = int(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))
+        kind = q % 3
+        if kind == 0:
+            n = max(10, n // 10 * 10)
+            e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
+        elif kind == 1:
+            e = synth.barabasi_albert(n, 2, rng)
+        else:
+            side = max(2, int(np.sqrt(n)))
+            n = side * side
+            e = synth.lattice(side, side)
+        xy = synth.uniform_positions(n, np.sqrt(n) / 2.0, rng)
+        out.append((n, e, xy))
+    return out
+
+
+@pytest.fixture(scope="module")
+def tfdp():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2303_03964_gb300 import tfdp as t
+    return t
+
+
+@pytest.mark.parametrize("grid_max", [255, 100])
+def test_batch_forces_equal_solo(tfdp, grid_max):
+    graphs = _mixed_graphs(9, 31 + grid_max)
+    params = [tfdp.params_default(grid_max=grid_max, gamma=2.0 + 0.5 * (q % 3)) for q in range(len(graphs))]
+    with tfdp.Batch(graphs, params) as b:
+        assert b.grid_blocks() > 0
+        for q, (n, e, xy) in enumerate(graphs):
+            fr_b, fa_b = b.eval_forces(q)
+            with tfdp.Graph(n, e, xy, params[q]) as g:
+                fr_s, fa_s = g.eval_forces()
+                st = g.stats()
+            assert _rel(fr_b, fr_s) <= FORCE_TOL, (q, _rel(fr_b, fr_s))
+            assert _rel(fa_b, fa_s) <= FORCE_TOL
+            if q < 3:
+                grid = oracle.grid_policy(xy, 3, 50, grid_max)
+                ref = oracle.rep_fft(xy.astype(np.float64), params[q].gamma, 3, grid=grid, xy_f32=xy)
+                assert _rel(fr_b, ref) <= FORCE_TOL
+            assert b.stats(q)["grid_G"] == st["grid_G"]
+
+
+def test_batch_layout_equals_solo(tfdp):
+    graphs = _mixed_graphs(6, 77, nmin=500, nmax=3000)
+    params = [tfdp.params_default(grid_max=255, total_iters=50) for _ in graphs]
+    T = 8
+    with tfdp.Batch(graphs, params) as b:
+        b.iterate(3)
+        b.iterate(T - 3)  # two launches (two captured graphs) in a row
+        for q, (n, e, xy) in enumerate(graphs):
+            out_b = b.get_positions(q)
+            assert b.stats(q)["iteration"] == T and b.stats(q)["device_flags"] == 0
+            with tfdp.Graph(n, e, xy, params[q]) as g:
+                g.iterate(T)
+                out_s = g.get_positions()
+            assert _rel(out_b, out_s) <= POS_TOL, (q, _rel(out_b, out_s))
+
+
+def test_batch_rejects_mixed_k_and_bad_graph(tfdp):
+    g1 = (10, [[0, 1]], np.zeros((10, 2), np.float32))
+    with pytest.raises(tfdp.TfdpError):
+        tfdp.Batch([g1, g1], [tfdp.params_default(k_interp=3), tfdp.params_default(k_interp=2)])
+    bad = (10, [[0, 0]], np.zeros((10, 2), np.float32))
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.Batch([g1, bad])
+    assert ei.value.status == 2
