@@ -121,6 +121,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    active = True  # nvidia-smi cannot be paused; it samples the whole measurement
+
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
@@ -172,6 +174,164 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+class NvmlSampler:
+    """SM clock, its maximum and the clock-event (throttle) reasons, read through NVML
+    every 2 ms in a background thread during the timed region (read-only queries)."""
+
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, cuda_index):
+        import ctypes
+        self.ok = False
+        self.samples = []
+        self.stop_flag = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            done = False
+            try:
+                import torch
+                uuid = str(torch.cuda.get_device_properties(cuda_index).uuid)
+                for cand in ("GPU-" + uuid, uuid):
+                    if lib.nvmlDeviceGetHandleByUUID(cand.encode(), ctypes.byref(h)) == 0:
+                        done = True
+                        break
+            except Exception:
+                pass
+            if not done and lib.nvmlDeviceGetHandleByIndex_v2(cuda_index, ctypes.byref(h)) != 0:
+                return
+            self.lib, self.h, self.ct = lib, h, ctypes
+            self.ok = True
+        except OSError:
+            pass
+
+    active = False  # samples are kept only while a timed region runs
+
+    def _read(self):
+        ct = self.ct
+        while not self.stop_flag:
+            if not self.active:
+                time.sleep(0.001)
+                continue
+            clk, mx, rs = ct.c_uint(0), ct.c_uint(0), ct.c_ulonglong(0)
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(clk)) == 0:
+                self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx))
+                fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                    self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+                fn(self.h, ct.byref(rs))
+                self.samples.append((clk.value, mx.value, rs.value))
+            time.sleep(0.002)
+
+    def start(self):
+        if self.ok:
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+
+    def stop(self):
+        if not self.ok:
+            return None
+        self.stop_flag = True
+        self.thread.join(timeout=2)
+        if not self.samples:
+            return None
+        reasons = set()
+        for _, _, r in self.samples:
+            for bit, name in self.REASONS.items():
+                if r & bit:
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(c for c, _, _ in self.samples),
+                "sm_max_mhz": max(m for _, m, _ in self.samples), "reasons": sorted(reasons),
+                "samples": len(self.samples), "source": "nvml every 2 ms inside the timed regions"}
+
+
+def serving_measurement(jobs=200, rate=20.0, updates=5, init_iters=300, upd_iters=50,
+                        budget_gb=48, max_active=24, chunk=10, sampler=None):
+    """Poisson stream of layout jobs (n log-uniform in [10k, 1M], SBM / BA in turn): each
+    job is laid out for init_iters iterations, then receives `updates` parameter changes
+    (alpha, beta, gamma uniform in the paper's ranges with alpha (1 + beta) < 1), each
+    followed by upd_iters warm-started iterations, submitted as soon as the previous
+    request of the job completes. Latency = completion - submission of a request."""
+    import numpy as np
+    from paper_2303_03964_gb300 import synth, tfdp
+    rng = synth.rng_for(5)
+    specs = []
+    t = 0.0
+    for q in range(jobs):
+        t += rng.exponential(1.0 / rate)
+        n = int(np.exp(rng.uniform(np.log(10_000), np.log(1_000_000)))) // 10 * 10
+        if q % 2 == 0:
+            e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
+        else:
+            e = synth.barabasi_albert(n, 3, rng)
+        xy = synth.uniform_positions(n, np.sqrt(n) / 2.0, rng)
+        # grid cap from the expected layout side (unit density): P = 1024 .. 2048
+        gmax = 3 * min(341, max(50, int(np.ceil(1.2 * np.sqrt(n)))))
+        ups = []
+        for _ in range(updates):
+            while True:
+                a, b = rng.uniform(0.01, 0.5), rng.uniform(8.0, 50.0)
+                if a * (1 + b) < 1:
+                    break
+            ups.append((a, b, float(rng.uniform(2.0, 8.0))))
+        specs.append((t, n, e, xy, gmax, ups))
+    total_n = sum(sp[1] for sp in specs)
+    srv = tfdp.Server(budget_gb << 30, max_active=max_active, chunk_iters=chunk)
+    job_of, pending, lat_upd, lat_init = {}, {}, [], []
+    n_of = {}
+    t0 = time.perf_counter()
+    if sampler is not None:
+        sampler.active = True
+    nxt, finished = 0, 0
+    first_submit = None
+    last_done = 0.0
+    while finished < jobs:
+        now = time.perf_counter() - t0
+        while nxt < jobs and specs[nxt][0] <= now:
+            _, n, e, xy, gmax, ups = specs[nxt]
+            job, _ = srv.submit(n, e, xy, tfdp.params_default(grid_max=gmax, total_iters=init_iters), init_iters)
+            job_of[job] = nxt
+            pending[job] = list(ups)
+            n_of[job] = n
+            nxt += 1
+        wait = 2 if nxt < jobs else 20
+        for d in srv.poll(256, wait_ms=wait):
+            job = d["job_id"]
+            if first_submit is None or d["t_submit"] < first_submit:
+                first_submit = d["t_submit"]
+            last_done = max(last_done, d["t_done"])
+            if d["status"] != 0:
+                raise RuntimeError("request failed: %s" % d)
+            (lat_init if d["kind"] == 0 else lat_upd).append(d["t_done"] - d["t_submit"])
+            if pending[job]:
+                a, b, g = pending[job].pop(0)
+                gmax = specs[job_of[job]][4]
+                srv.update(job, tfdp.params_default(alpha=a, beta=b, gamma=g, grid_max=gmax), upd_iters)
+            else:
+                srv.release(job)
+                finished += 1
+    if sampler is not None and isinstance(sampler, NvmlSampler):
+        sampler.active = False
+    st = srv.stats()
+    srv.close()
+    span = last_done - first_submit
+    node_its = total_n * (init_iters + updates * upd_iters)
+
+    def pct(v, q):
+        v = sorted(v)
+        return v[min(len(v) - 1, int(q * len(v)))]
+    return {"workload": "%d jobs, Poisson %.0f/s, n log-uniform in [10k, 1M] (sum %d), SBM / BA m0=3 in turn; "
+                        "%d-iteration layout then %d updates of %d warm-started iterations" % (
+                            jobs, rate, total_n, init_iters, updates, upd_iters),
+            "update_latency_s_p50": pct(lat_upd, 0.5), "update_latency_s_p99": pct(lat_upd, 0.99),
+            "layout_latency_s_p50": pct(lat_init, 0.5), "layout_latency_s_p99": pct(lat_init, 0.99),
+            "throughput": node_its / span, "unit": UNIT, "span_s": span, "requests": len(lat_upd) + len(lat_init),
+            "peak_active_jobs": st["peak_active"], "budget_bytes": st["budget_bytes"], "max_active": max_active,
+            "chunk_iters": chunk}
+
+
 def cpu_baseline(e, xy, spec, budget_s=15.0):
     """The FP64 oracle as it stands, on the same workload, on this host's cores."""
     import numpy as np
@@ -193,7 +353,7 @@ def cpu_baseline(e, xy, spec, budget_s=15.0):
                 iters, mode, el)}
 
 
-def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48):
+def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, sampler=None):
     """512 mixed graphs (n log-uniform in [1k, 50k]) advanced by one persistent launch
     per batch iteration, against the same graphs run one at a time (a sample of them)."""
     import torch
@@ -217,7 +377,11 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48):
 
     for _ in range(warmup):
         timed(lambda: b.iterate(1))
+    if sampler is not None:
+        sampler.active = True
     ms = [timed(lambda: b.iterate(1)) for _ in range(steps)]
+    if sampler is not None and isinstance(sampler, NvmlSampler):
+        sampler.active = False
     flags = max(b.stats(q)["device_flags"] for q in (0, len(graphs) // 2, len(graphs) - 1))
     b.close()
     # solo: a sample of the same graphs, one graph per launch sequence
@@ -322,15 +486,19 @@ def run_ours(args):
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
-    sampler = ClockSampler(local)
+    sampler = NvmlSampler(local)
+    if not sampler.ok:
+        sampler = ClockSampler(local)
     sampler.start()
+    sampler.active = True
     step_ms, stages = [], []
     for _ in range(args.steps):
         ms, st = step()
         step_ms.append(ms)
         stages.append(st)
     torch.cuda.synchronize()
-    clocks = sampler.stop()
+    if isinstance(sampler, NvmlSampler):
+        sampler.active = False
     total_ms = sum(step_ms)
     if ws > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -388,7 +556,11 @@ def run_ours(args):
         cpu = cpu_baseline(e, xy, spec)
     batched = None
     if not args.no_batch and args.workload == "lattice_1m":
-        batched = batched_measurement(args, stream, flush, args.steps, args.warmup)
+        batched = batched_measurement(args, stream, flush, args.steps, args.warmup, sampler=sampler)
+    serving = None
+    if not args.no_serving and args.workload == "lattice_1m":
+        serving = serving_measurement(sampler=sampler)
+    clocks = sampler.stop()
     value = ws * n * args.steps / (total_ms * 1e-3)
     q = sorted(step_ms)
     line = {
@@ -403,6 +575,7 @@ def run_ours(args):
         "step_ms_p50": q[len(q) // 2], "step_ms_p99": q[min(len(q) - 1, int(0.99 * len(q)))],
         "mixed": None,
         "batched": batched,
+        "serving": serving,
         "stages_ms": mean_stage,
         "roofline": roof,
         "cpu_baseline": cpu,
@@ -428,6 +601,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lattice_1m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -152,28 +152,36 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
 #pragma unroll
         for (int lx = 0; lx < K; ++lx) rho[ly][lx] = mx[ly][lx] = my[ly][lx] = 0;
     const float inv_h = 1.0f / ag.h_hi;
-    for (int s = s0; s < s1; ++s) {
-        const float2 p = sxy[s];
-        float ox, oy;
-        box_offset(p.x, ag, &ox);
-        box_offset(p.y, ag, &oy);
-        float wx[K], wy[K], dx[K], dy[K];
-        lagrange<K>(ox / ag.h_hi, wx);
-        lagrange<K>(oy / ag.h_hi, wy);
+    // two nodes per round: both loads are in flight before either is used
+    for (int s = s0; s < s1; s += 2) {
+        const bool two = s + 1 < s1;
+        float2 pp[2];
+        pp[0] = sxy[s];
+        pp[1] = two ? sxy[s + 1] : pp[0];
 #pragma unroll
-        for (int l = 0; l < K; ++l) {
-            dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
-            dy[l] = (oy - ((float)l + 0.5f) * ag.hk) * inv_h;
-        }
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+            float ox, oy;
+            box_offset(pp[u].x, ag, &ox);
+            box_offset(pp[u].y, ag, &oy);
+            float wx[K], wy[K], dx[K], dy[K];
+            lagrange<K>(ox / ag.h_hi, wx);
+            lagrange<K>(oy / ag.h_hi, wy);
 #pragma unroll
-        for (int ly = 0; ly < K; ++ly)
-#pragma unroll
-            for (int lx = 0; lx < K; ++lx) {
-                const float w = wx[lx] * wy[ly];
-                rho[ly][lx] += spread_q(w);
-                mx[ly][lx] += spread_q(w * dx[lx]);
-                my[ly][lx] += spread_q(w * dy[ly]);
+            for (int l = 0; l < K; ++l) {
+                dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
+                dy[l] = (oy - ((float)l + 0.5f) * ag.hk) * inv_h;
             }
+#pragma unroll
+            for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+                for (int lx = 0; lx < K; ++lx) {
+                    const float w = wx[lx] * wy[ly];
+                    rho[ly][lx] += spread_q(w);
+                    mx[ly][lx] += spread_q(w * dx[lx]);
+                    my[ly][lx] += spread_q(w * dy[ly]);
+                }
+        }
     }
     const float hs = ag.h_hi * kSpreadInvScale;
 #pragma unroll

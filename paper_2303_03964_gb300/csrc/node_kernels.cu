@@ -340,24 +340,41 @@ __global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a, in
     const float step = (float)st->step_cur;
     float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
     unsigned bad = 0;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < a.n; s += gridDim.x * blockDim.x) {
-        const float2 p = sxy[s];
-        const int i = perm[s];
-        if ((unsigned)i >= (unsigned)a.n) continue;  // only after a failed sort (flagged there)
-        const float2 fa = a.fatt_out[i];
-        const float2 fg = gather_frep<K>(p, ag, a.gout, a.Gs);
-        const float frx = fg.x, fry = fg.y;
-        sfx += frx;
-        sfy += fry;
-        if (EVAL) {
-            a.frep_out[i] = make_float2(frx, fry);
-        } else {
-            const float2 q = capped_step(p, make_float2(frx + fa.x, fry + fa.y), step);
-            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
-            xout[i] = q;
-            sxy[s] = q;  // next iteration's visit order is this iteration's sorted order
-            mn = fminf(mn, fminf(q.x, q.y));
-            mx = fmaxf(mx, fmaxf(q.x, q.y));
+    // two sorted slots per thread per round (base and base + blockDim) so that the
+    // dependent loads of both nodes overlap
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+        const int ss[2] = {base, base + (int)blockDim.x};
+        float2 p[2], fa[2];
+        int ii[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = ss[u] < a.n ? ss[u] : base;
+            p[u] = sxy[s];
+            ii[u] = perm[s];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            fa[u] = ((unsigned)ii[u] < (unsigned)a.n) ? a.fatt_out[ii[u]] : make_float2(0.f, 0.f);
+        float2 fr[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) fr[u] = gather_frep<K>(p[u], ag, a.gout, a.Gs);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = ss[u], i = ii[u];
+            if (s >= a.n || (unsigned)i >= (unsigned)a.n) continue;  // bad ids only after a failed sort
+            sfx += fr[u].x;
+            sfy += fr[u].y;
+            if (EVAL) {
+                a.frep_out[i] = fr[u];
+            } else {
+                const float2 q = capped_step(p[u], make_float2(fr[u].x + fa[u].x, fr[u].y + fa[u].y), step);
+                if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+                xout[i] = q;
+                sxy[s] = q;  // next iteration's visit order is this iteration's sorted order
+                mn = fminf(mn, fminf(q.x, q.y));
+                mx = fmaxf(mx, fmaxf(q.x, q.y));
+            }
         }
     }
     if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
@@ -563,7 +580,7 @@ cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s) {
 }
 
 cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
-    const int nb = blocks_for(a.n, kNodeThreads);
+    const int nb = blocks_for(a.n, 2 * kNodeThreads);
     switch (a.k) {
         case 1: eval ? k_gather_update<1, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<1, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
         case 2: eval ? k_gather_update<2, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<2, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
