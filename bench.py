@@ -45,9 +45,27 @@ WORKLOADS = {
                       "rep": "exact", "k": 3, "grid_max": 255, "total_iters": 100},
 }
 
-# DRAM bytes of the dominant kernel from one ncu capture, per launch, keyed by stage,
-# valid only while the kernel source is unchanged (sha256 of the file that defines it).
-NCU_TRAFFIC = {}
+# DRAM bytes of the dominant kernel from one ncu capture, per launch, keyed by
+# (workload, stage); valid only while every source file the kernel is built from is
+# unchanged (sha256 over STAGE_SOURCES). Captured with
+#   ncu --set full --clock-control none -k regex:k_cols_r -s 2 -c 1 -o prof_k_cols_r
+#       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-batch --no-serving
+NCU_TRAFFIC = {
+    ("lattice_1m", "cols"): {"bytes": 50455552 + 1035264, "sha": "e65fe3260f3c8115"},
+}
+
+# Stages timed by the library that are ONE kernel on the critical path, and that kernel
+# (P <= 4096 uses the register-resident FFT kernels). "sort" is four kernels (grid, bin,
+# scan, scatter) and "attract" runs on a side stream under the FFT, so neither is a
+# roofline candidate.
+STAGE_KERNEL = {"spread": "k_spread", "rows_fwd": "k_rows_fwd_r", "cols": "k_cols_r",
+                "rows_inv": "k_rows_inv_r", "gather_update": "k_gather_update",
+                "exact": "k_exact", "edge_update": "k_edge_update"}
+
+_NODE_SRC = ("node_kernels.cu", "node_dev.cuh", "common.cuh", "launch.h")
+_FFT_SRC = ("fft_kernels.cu", "fft_stages.cuh", "fft_reg.cuh", "fft.cuh", "common.cuh", "launch.h")
+STAGE_SOURCES = {"spread": _NODE_SRC, "gather_update": _NODE_SRC, "edge_update": _NODE_SRC,
+                 "exact": _NODE_SRC, "rows_fwd": _FFT_SRC, "cols": _FFT_SRC, "rows_inv": _FFT_SRC}
 
 
 def make_workload(name):
@@ -89,20 +107,15 @@ def stage_bytes(stage, n, m, G, P, nbox):
     return 0
 
 
-def stage_source(stage):
-    return {"sort": "node_kernels.cu", "spread": "node_kernels.cu",
-            "gather_update": "node_kernels.cu", "edge_update": "node_kernels.cu",
-            "exact": "node_kernels.cu", "rows_fwd": "fft_kernels.cu", "cols": "fft_kernels.cu",
-            "rows_inv": "fft_kernels.cu", "spectrum": "fft_kernels.cu"}.get(stage)
-
-
 def source_sha(stage):
-    src = stage_source(stage)
-    if not src:
+    srcs = STAGE_SOURCES.get(stage)
+    if not srcs:
         return None
-    path = os.path.join(ROOT, "paper_2303_03964_gb300", "csrc", src)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(os.path.join(ROOT, "paper_2303_03964_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -406,10 +419,8 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2303_03964_gb300 import replicas
+    return replicas.world()
 
 
 def run_reference(args):
@@ -457,7 +468,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2303_03964_gb300 import tfdp
+    from paper_2303_03964_gb300 import replicas, tfdp
 
     spec = WORKLOADS[args.workload]
     e, xy = make_workload(args.workload)
@@ -484,8 +495,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     sampler = NvmlSampler(local)
     if not sampler.ok:
         sampler = ClockSampler(local)
@@ -497,14 +507,11 @@ def run_ours(args):
         step_ms.append(ms)
         stages.append(st)
     torch.cuda.synchronize()
+    replicas.barrier()
     if isinstance(sampler, NvmlSampler):
         sampler.active = False
-    total_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.barrier()
-        total_ms = float(t.item())
+    # replicas: every rank ran the same workload; the slowest rank's time counts
+    total_ms = replicas.max_over_ranks(sum(step_ms))
     stats = g.stats()
 
     # end to end through the C ABI with host buffers: pinned positions in and out
@@ -520,11 +527,7 @@ def run_ours(args):
         g.get_positions(host_out.numpy())
         e2e_s.append(time.perf_counter() - t0)
         host_in.copy_(host_out)
-    e2e_total = sum(e2e_s)
-    if ws > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = replicas.max_over_ranks(sum(e2e_s))
 
     if rank != 0:
         g.close()
@@ -535,20 +538,22 @@ def run_ours(args):
     mean_stage = {k: statistics.fmean(s[k] for s in stages) for k in stages[0]}
     G, P = stats["grid_G"], stats["fft_P"]
     nbox = stats["grid_n_int"] ** 2
-    cand = {k: v for k, v in mean_stage.items() if v > 0 and k != "spectrum"}
+    cand = {k: v for k, v in mean_stage.items() if v > 0 and k in STAGE_KERNEL}
     dom = max(cand, key=cand.get)
     peak, peak_kind = measured_peaks()
     roof = None
     if dom == "exact":
         flops = 11.0 * n * n
-        roof = {"stage": dom, "bound": "alu", "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+        roof = {"stage": dom, "kernel": STAGE_KERNEL[dom], "bound": "alu",
+                "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
                 "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
     else:
         bytes_ = stage_bytes(dom, n, m, G, P, nbox)
         ach = bytes_ / (mean_stage[dom] * 1e-3) / 1e9
         tr = NCU_TRAFFIC.get((args.workload, dom))
         traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(dom) else None
-        roof = {"stage": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+        roof = {"stage": dom, "kernel": STAGE_KERNEL[dom], "bound": "hbm", "achieved": ach, "peak": peak,
+                "unit": "GB/s",
                 "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": bytes_,
                 "peak_kind": peak_kind + " hbm_gbs (burst copy)"}
     cpu = None

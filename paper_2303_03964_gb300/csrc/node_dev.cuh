@@ -97,13 +97,16 @@ __device__ __forceinline__ float2 capped_step(float2 p, float2 D, float s) {
 
 // The grid of iteration t = st->iter from the layout extremes (exact FP64 decisions),
 // the step s_t, the spectrum key and the bookkeeping of the iteration (one thread).
-__device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, int advance) {
+// with_step = false leaves st->step_cur to the caller (k_grid fetches it on another lane).
+__device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, int advance, bool with_step = true) {
+    // both bbox slots are loaded with the counter, so no load waits on another
+    const unsigned b00 = st->bbox[0][0], b01 = st->bbox[0][1], b10 = st->bbox[1][0], b11 = st->bbox[1][1];
     const long long t = st->iter;
     const int cur = (int)(t & 1);
-    const GridDesc g = make_grid(ord2f(st->bbox[cur][0]), ord2f(st->bbox[cur][1]), prm);
+    const GridDesc g = make_grid(ord2f(cur ? b10 : b00), ord2f(cur ? b11 : b01), prm);
     st->grid = g;
     st->t_cur = t;
-    st->step_cur = step_size(t, prm);
+    if (with_step) st->step_cur = step_size(t, prm);
     st->net_frep[0] = 0.0;
     st->net_frep[1] = 0.0;
     if (advance) {
@@ -137,6 +140,18 @@ __device__ __forceinline__ long long spread_q(float v) {
     // round to nearest; NaN -> 0 and saturation keep the conversion defined
     const float s = fminf(fmaxf(v * kSpreadScale, -2.0e9f), 2.0e9f);
     return (long long)__float2int_rn(s);
+}
+
+// int64 -> FP32 rounded to nearest even, equal to (float)v. The 64-bit conversion
+// instruction issues on the FP64 pipe (ncu: that pipe was 57% busy in a spread kernel
+// with no FP64 arithmetic), so for |v| < 2^48 the value is split as v = hi 2^24 + lo,
+// both halves exact in FP32, and one FP32 addition rounds the exact sum once.
+__device__ __forceinline__ float ll2f_rn(long long v) {
+    const long long hi = v >> 24;           // floor(v / 2^24)
+    const int lo = (int)(v & 0xFFFFFFLL);   // 0 .. 2^24 - 1
+    if (hi >= -(1LL << 24) && hi < (1LL << 24))
+        return __fadd_rn(__int2float_rn((int)hi) * 16777216.0f, __int2float_rn(lo));
+    return __ll2float_rn(v);
 }
 
 // Lagrange projection (Sec. 3.4 step 1) of the nodes sxy[s0, s1) of box (bx, by) onto its
@@ -189,9 +204,9 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
 #pragma unroll
         for (int lx = 0; lx < K; ++lx) {
             const size_t q = (size_t)(by * K + ly) * Gs + (bx * K + lx);
-            gin[q] = (float)rho[ly][lx] * kSpreadInvScale;
-            gin[plane + q] = (float)mx[ly][lx] * hs;
-            gin[2 * plane + q] = (float)my[ly][lx] * hs;
+            gin[q] = ll2f_rn(rho[ly][lx]) * kSpreadInvScale;
+            gin[plane + q] = ll2f_rn(mx[ly][lx]) * hs;
+            gin[2 * plane + q] = ll2f_rn(my[ly][lx]) * hs;
         }
 }
 

@@ -28,6 +28,7 @@ namespace tfdp {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
+static_assert(kScanItems == 8, "k_scan_lookback moves its items as two int4");
 constexpr int kNodeThreads = 256;
 
 int scan_items_per_block() { return kScanChunk; }
@@ -103,9 +104,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict_
 // ---------------------------------------------------------------- FFT path: grid
 // One thread: the grid of this iteration from the layout extremes (exact FP64
 // decisions), the step s_t, the spectrum key, and the bookkeeping of the iteration.
+// Lane 1 fetches s_t from the step table while lane 0 decides the grid, so the table's
+// dependent load overlaps the FP64 work.
 __global__ void k_grid(NodeLaunch a, int advance) {
+    if (threadIdx.x == 1) {
+        a.st->step_cur = step_size(a.st->iter, *a.prm);
+        return;
+    }
     if (threadIdx.x != 0) return;
-    grid_decide(a.st, *a.prm, advance);
+    const DevParams prm = *a.prm;
+    grid_decide(a.st, prm, advance, false);
 }
 
 // Box of every node (the FP32 decision) and its slot in the box (counting-sort
@@ -247,13 +255,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
     }
     __syncthreads();
     int run = s_prefix + s_w[w] + incl - tsum;
+    int o[kScanItems];
 #pragma unroll
     for (int q = 0; q < kScanItems; ++q) {
-        if (i0 + q < nbox) {
-            a.off[i0 + q] = run;
-            a.cnt[i0 + q] = 0;  // ready for the next histogram
-        }
+        o[q] = run;
         run += v[q];
+    }
+    // cnt holds ntiles * kScanChunk counters (zero past nbox), off is 256-byte aligned and
+    // i0 a multiple of 8: full rows go out as two 16-byte stores
+    int4* cz = reinterpret_cast<int4*>(a.cnt + i0);
+    cz[0] = make_int4(0, 0, 0, 0);  // ready for the next histogram
+    cz[1] = make_int4(0, 0, 0, 0);
+    if (i0 + kScanItems <= nbox) {
+        int4* od = reinterpret_cast<int4*>(a.off + i0);
+        od[0] = make_int4(o[0], o[1], o[2], o[3]);
+        od[1] = make_int4(o[4], o[5], o[6], o[7]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kScanItems; ++q)
+            if (i0 + q < nbox) a.off[i0 + q] = o[q];
     }
     // off[nbox] = n, written by the thread whose items end at or contain nbox
     if (i0 <= nbox && (nbox < i0 + kScanItems || (nbox == i0 + kScanItems && i0 + kScanItems == ntiles * kScanChunk)))

@@ -167,6 +167,25 @@ def test_fft_forces_lattice_1m_full_size(tfdp):
     assert abs(interp_err - ref_err) <= 1e-3 * ref_err + FORCE_TOL
 
 
+def test_fft_forces_lattice_1m_at_oracle_50_iterations(tfdp):
+    """Config 3 (i), second snapshot: the force field at the oracle's own layout after 50
+    iterations (k=3, grid up to 1023, SNAP_H, P=2048, 300-iteration schedule), rounded
+    to FP32, so that the grid, the box occupancy and the spectrum are those of a
+    contracting layout rather than of the uniform start."""
+    e, xy = synth.lattice_1m()
+    n = xy.shape[0]
+    x50 = oracle.iterate(xy.astype(np.float64), e, 50, mode="fft", k=3, grid_max=1023,
+                         policy=oracle.GRID_SNAP_H, P=2048, T=300).astype(np.float32)
+    with tfdp.Graph(n, e, x50, _params(tfdp, grid_max=1023)) as g:
+        fr, fa = g.eval_forces()
+        st = g.stats()
+    assert st["fft_P"] == 2048
+    _, ref = _oracle_fft(x50, st, 2.0, 3, 1023, 1)
+    assert record("fft_lattice1m_it50_frep", rel_l2(fr, ref)) <= FORCE_TOL
+    assert record("fft_lattice1m_it50_fatt",
+                  rel_l2(fa, oracle.attraction(e, x50.astype(np.float64), 0.1, 8.0))) <= FORCE_TOL
+
+
 def test_fft_ba_2m_full_size(tfdp):
     """Config 3 (ii): Barabasi-Albert n=2M, m0=3 (heavy-tailed degrees)."""
     e, xy = synth.ba_2m()
