@@ -83,6 +83,20 @@ struct RegGeom {
     static constexpr size_t cols_smem = (size_t)CG * 3 * P * sizeof(float2);
 };
 
+// Frequency kx handled by split index j (0 <= j <= P/2) in the half-spectrum passes of
+// the row kernels: a bijection that gives the lanes of a warp frequencies P/64 apart.
+// Their digit-reversed positions (pos_of_freq) then differ in the low digits, i.e. fall
+// in different shared-memory banks; consecutive frequencies would all share one bank
+// pair, since the swizzle only mixes the low digits.
+template <int LOGP>
+__device__ __forceinline__ int split_freq(int j) {
+    static_assert(LOGP >= 6, "split_freq needs P / 2 to be a multiple of 32");
+    constexpr int H = 1 << (LOGP - 1);  // P / 2
+    if (j >= H) return j;               // the Nyquist bin
+    constexpr int R = H / 32;
+    return (j & 31) * R + (j >> 5);
+}
+
 // Forward row transforms of row block `blk` (2 RG rows x 3 channels) of a source into
 // out[c][kx][ystride] (half spectrum along x, column-major).
 template <int LOGP, class Src>
@@ -114,7 +128,7 @@ __device__ __forceinline__ void rows_fwd_body(const Src& src, int nrows, int blk
     // 2 RG consecutive rows (RG row pairs) of out[c][kx][.]
     for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
         const int c = idx / NH;
-        const int kx = idx - c * NH;
+        const int kx = split_freq<LOGP>(idx - c * NH);
         const int pk = swz(pos_of_freq<LOGP>(kx));
         const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
         float4* dst = reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + ybase);
@@ -229,7 +243,7 @@ __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict_
     // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum
     for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
         const int c = idx / NH;
-        const int kx = idx - c * NH;
+        const int kx = split_freq<LOGP>(idx - c * NH);
         const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
         const int pk = swz(pos_of_freq<LOGP>(kx));
         const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));

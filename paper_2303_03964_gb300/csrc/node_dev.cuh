@@ -26,11 +26,8 @@ __device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g) {
     return a;
 }
 
-// Box index b (the FP32 decision shared with the oracle) and the offset of x from the
-// box origin lo + b h, accurate to a few ulps of h.
-__device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off) {
-    float tq;
-    const int b = box_of(x, a.lo, a.h_hi, a.n_int, &tq);
+// Offset of x from the origin lo + b h of box b, accurate to a few ulps of h.
+__device__ __forceinline__ float box_offset_at(float x, int b, const AxisGeom& a) {
     // x - lo = s + e exactly (TwoSum)
     const float s = __fsub_rn(x, a.lo);
     const float bb = __fsub_rn(s, x);
@@ -39,7 +36,15 @@ __device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off
     const float fb = (float)b;
     const float p = __fmul_rn(fb, a.h_hi);
     const float pe = __fmaf_rn(fb, a.h_hi, -p);
-    *off = __fadd_rn(__fsub_rn(s, p), __fsub_rn(__fsub_rn(e, pe), __fmul_rn(fb, a.h_lo)));
+    return __fadd_rn(__fsub_rn(s, p), __fsub_rn(__fsub_rn(e, pe), __fmul_rn(fb, a.h_lo)));
+}
+
+// Box index b (the FP32 decision shared with the oracle) and the offset of x from the
+// box origin lo + b h.
+__device__ __forceinline__ int box_offset(float x, const AxisGeom& a, float* off) {
+    float tq;
+    const int b = box_of(x, a.lo, a.h_hi, a.n_int, &tq);
+    *off = box_offset_at(x, b, a);
     return b;
 }
 
@@ -137,20 +142,23 @@ constexpr float kSpreadScale = 134217728.0f;       // 2^27
 constexpr float kSpreadInvScale = 1.0f / 134217728.0f;
 
 __device__ __forceinline__ long long spread_q(float v) {
-    // round to nearest; NaN -> 0 and saturation keep the conversion defined
-    const float s = fminf(fmaxf(v * kSpreadScale, -2.0e9f), 2.0e9f);
-    return (long long)__float2int_rn(s);
+    // round to nearest even; a float-to-integer conversion saturates to the int32 range
+    // by itself (in-box terms stay below 2^30), so no clamp is needed to keep it defined
+    return (long long)__float2int_rn(v * kSpreadScale);
 }
 
-// int64 -> FP32 rounded to nearest even, equal to (float)v. The 64-bit conversion
-// instruction issues on the FP64 pipe (ncu: that pipe was 57% busy in a spread kernel
-// with no FP64 arithmetic), so for |v| < 2^48 the value is split as v = hi 2^24 + lo,
-// both halves exact in FP32, and one FP32 addition rounds the exact sum once.
+// int64 -> FP32 rounded to nearest even, equal to (float)v, in 32-bit integer and FP32
+// operations only. For |v| < 2^48 (every sum a box of fewer than ~10^5 nodes produces)
+// v = h 2^24 + lo with h, lo exact in FP32, and one FP32 addition rounds the exact sum
+// once; larger values take the library conversion.
 __device__ __forceinline__ float ll2f_rn(long long v) {
-    const long long hi = v >> 24;           // floor(v / 2^24)
-    const int lo = (int)(v & 0xFFFFFFLL);   // 0 .. 2^24 - 1
-    if (hi >= -(1LL << 24) && hi < (1LL << 24))
-        return __fadd_rn(__int2float_rn((int)hi) * 16777216.0f, __int2float_rn(lo));
+    const unsigned lo32 = (unsigned)v;
+    const int hi32 = (int)((unsigned long long)v >> 32);
+    if (hi32 >= -(1 << 16) && hi32 < (1 << 16)) {                  // -2^48 <= v < 2^48
+        const int h = (int)__funnelshift_r(lo32, (unsigned)hi32, 24);  // v >> 24
+        const int lo = (int)(lo32 & 0xFFFFFFu);                        // v mod 2^24
+        return __fadd_rn(__int2float_rn(h) * 16777216.0f, __int2float_rn(lo));
+    }
     return __ll2float_rn(v);
 }
 
@@ -176,12 +184,13 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (u == 1 && !two) break;
-            float ox, oy;
-            box_offset(pp[u].x, ag, &ox);
-            box_offset(pp[u].y, ag, &oy);
+            // the node's box is (bx, by): the sort placed it there by the same FP32
+            // decision, so only the offsets are formed here
+            const float ox = box_offset_at(pp[u].x, bx, ag);
+            const float oy = box_offset_at(pp[u].y, by, ag);
             float wx[K], wy[K], dx[K], dy[K];
-            lagrange<K>(ox / ag.h_hi, wx);
-            lagrange<K>(oy / ag.h_hi, wy);
+            lagrange<K>(ox * inv_h, wx);
+            lagrange<K>(oy * inv_h, wy);
 #pragma unroll
             for (int l = 0; l < K; ++l) {
                 dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
@@ -217,9 +226,10 @@ __device__ __forceinline__ float2 gather_frep(float2 p, const AxisGeom& ag, cons
     float ox, oy;
     const int bx = box_offset(p.x, ag, &ox);
     const int by = box_offset(p.y, ag, &oy);
+    const float inv_h = 1.0f / ag.h_hi;
     float wx[K], wy[K], dx[K], dy[K];
-    lagrange<K>(ox / ag.h_hi, wx);
-    lagrange<K>(oy / ag.h_hi, wy);
+    lagrange<K>(ox * inv_h, wx);
+    lagrange<K>(oy * inv_h, wy);
 #pragma unroll
     for (int l = 0; l < K; ++l) {
         dx[l] = ox - ((float)l + 0.5f) * ag.hk;

@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
 // One thread per box: sum over the box's nodes (contiguous after the sort) of the
 // Lagrange weights w (rho) and of w times the offset to each grid node (m^x, m^y).
 template <int K>
-__global__ void __launch_bounds__(kNodeThreads) k_spread(NodeLaunch a) {
+__global__ void __launch_bounds__(kNodeThreads, 3) k_spread(NodeLaunch a) {
     const GridDesc g = a.st->grid;
     const int nbox = g.n_int * g.n_int;
     const AxisGeom ag = axis_geom(g);
