@@ -51,7 +51,7 @@ WORKLOADS = {
 #   ncu --set full --clock-control none -k regex:k_cols_r -s 2 -c 1 -o prof_k_cols_r
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-batch --no-serving
 NCU_TRAFFIC = {
-    ("lattice_1m", "cols"): {"bytes": 50455552 + 1035264, "sha": "e65fe3260f3c8115"},
+    ("lattice_1m", "cols"): {"bytes": 50456064 + 1078016, "sha": "33796e5d3386f80f"},
 }
 
 # Stages timed by the library that are ONE kernel on the critical path, and that kernel
@@ -478,6 +478,7 @@ def run_ours(args):
                                  total_iters=spec["total_iters"])
     stream = torch.cuda.Stream()
     g = tfdp.Graph(n, e, xy, params, stream=stream.cuda_stream)
+    # warm-up with every stage bracketed by events, to find the dominant single kernel
     g.set_stage_timing(True)
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -492,7 +493,13 @@ def run_ours(args):
         stream.synchronize()
         return ev0.elapsed_time(ev1), g.stage_times()
 
-    for _ in range(args.warmup):
+    warm = [step()[1] for _ in range(args.warmup)]
+    cand = {k: statistics.fmean(w[k] for w in warm[-2:]) for k in STAGE_KERNEL}
+    dom = max(cand, key=cand.get)
+    # the timed steps bracket only that kernel (the library records the events on a
+    # side branch of the captured iteration, so they cost the step < 1 us)
+    g.set_stage_timing_mask([dom])
+    for _ in range(2):  # the iteration graph is recaptured with the new event set
         step()
     torch.cuda.synchronize()
     replicas.barrier()
@@ -535,26 +542,28 @@ def run_ours(args):
             torch.distributed.destroy_process_group()
         return 0
 
-    mean_stage = {k: statistics.fmean(s[k] for s in stages) for k in stages[0]}
+    dom_ms = statistics.fmean(st[dom] for st in stages)
+    # per-stage breakdown, outside the timed region, with every stage bracketed
+    g.set_stage_timing(True)
+    brk = [step()[1] for _ in range(5)][2:]
+    mean_stage = {k: statistics.fmean(b[k] for b in brk) for k in brk[0]}
     G, P = stats["grid_G"], stats["fft_P"]
     nbox = stats["grid_n_int"] ** 2
-    cand = {k: v for k, v in mean_stage.items() if v > 0 and k in STAGE_KERNEL}
-    dom = max(cand, key=cand.get)
     peak, peak_kind = measured_peaks()
     roof = None
     if dom == "exact":
         flops = 11.0 * n * n
         roof = {"stage": dom, "kernel": STAGE_KERNEL[dom], "bound": "alu",
-                "achieved": flops / (mean_stage[dom] * 1e-3) / 1e12,
+                "achieved": flops / (dom_ms * 1e-3) / 1e12, "kernel_ms": dom_ms,
                 "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None}
     else:
         bytes_ = stage_bytes(dom, n, m, G, P, nbox)
-        ach = bytes_ / (mean_stage[dom] * 1e-3) / 1e9
+        ach = bytes_ / (dom_ms * 1e-3) / 1e9
         tr = NCU_TRAFFIC.get((args.workload, dom))
         traffic = tr["bytes"] if tr and tr.get("sha") == source_sha(dom) else None
         roof = {"stage": dom, "kernel": STAGE_KERNEL[dom], "bound": "hbm", "achieved": ach, "peak": peak,
                 "unit": "GB/s",
-                "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": bytes_,
+                "frac": ach / peak, "traffic": traffic, "algorithmic_bytes": bytes_, "kernel_ms": dom_ms,
                 "peak_kind": peak_kind + " hbm_gbs (burst copy)"}
     cpu = None
     if not args.no_cpu_baseline and ws >= 1 and rank == 0:
@@ -582,6 +591,8 @@ def run_ours(args):
         "batched": batched,
         "serving": serving,
         "stages_ms": mean_stage,
+        "stages_note": "5 steps after the timed region with every stage bracketed by events "
+                       "(the timed steps bracket only the roofline kernel)",
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": ws * n * args.steps / e2e_total, "unit": UNIT,

@@ -119,10 +119,14 @@ struct tfdp_graph {
     cudaGraphExec_t exec1 = nullptr, execB = nullptr;
     long long exec_key = -1;
 
-    // stage timing (events around the stages of an iteration)
-    bool timing = false;
-    cudaEvent_t ev[TFDP_NUM_STAGES + 1] = {};
-    cudaEvent_t ev_attract[2] = {};
+    // stage timing: begin / end events around the stages whose bit is set in timing_mask
+    unsigned timing_mask = 0;
+    cudaEvent_t ev_b[TFDP_NUM_STAGES] = {}, ev_e[TFDP_NUM_STAGES] = {};
+    // the timing events are recorded on their own stream, forked at each stage border and
+    // joined at the end of the iteration, so the kernel chain has no event node in it
+    cudaStream_t time_stream = nullptr;
+    cudaEvent_t time_fork[2 * TFDP_NUM_STAGES] = {};
+    cudaEvent_t time_join = nullptr;
 
     // side stream for the attraction of the FFT path (fork / join events)
     cudaStream_t side_stream = nullptr;
@@ -349,48 +353,70 @@ tfdp_status refresh_bbox(tfdp_graph* g) {
 }
 
 // Enqueue one iteration (advance = 1) or one force evaluation (advance = 0, eval = 1).
-// With stage timing on, an event is recorded before the first stage and after each
-// stage (inside a captured graph these become event-record nodes).
+// Stages selected by the timing mask are bracketed by event records. The records sit on
+// a branch of their own (forked from the stage's stream at each border, joined at the
+// end), so no kernel waits for one; inside a captured graph they become event-record
+// nodes off the kernel chain.
 tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
     const NodeLaunch a = g->node_launch();
-    const bool tm = g->timing;
-    int mark_i = 0;
+    const unsigned tm = g->timing_mask;
     // cudaEventRecordExternal makes the record a node of a captured graph (a plain
     // record inside a capture only orders the capture and is never timed)
-    auto mark = [&]() -> cudaError_t {
-        return tm ? cudaEventRecordWithFlags(g->ev[mark_i++], s, cudaEventRecordExternal) : cudaSuccess;
+    auto stamp = [&](cudaEvent_t ev, cudaEvent_t fork, cudaStream_t st) -> cudaError_t {
+        cudaError_t e = cudaEventRecord(fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g->time_stream, fork, 0);
+        if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev, g->time_stream, cudaEventRecordExternal);
+        return e;
     };
-    CK(mark());
+    auto begin = [&](int stage, cudaStream_t st) -> cudaError_t {
+        return ((tm >> stage) & 1u) ? stamp(g->ev_b[stage], g->time_fork[2 * stage], st) : cudaSuccess;
+    };
+    auto end = [&](int stage, cudaStream_t st) -> cudaError_t {
+        return ((tm >> stage) & 1u) ? stamp(g->ev_e[stage], g->time_fork[2 * stage + 1], st) : cudaSuccess;
+    };
     if (g->params.rep_mode == TFDP_REP_EXACT) {
+        CK(begin(TFDP_STAGE_EXACT, s));
         CK(launch_exact_pairs(a, advance, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_EXACT, s));
+        CK(begin(TFDP_STAGE_EDGE_UPDATE, s));
         CK(launch_edge_update(a, advance, eval, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_EDGE_UPDATE, s));
     } else {
         const FftLaunch f = g->fft_launch();
+        CK(begin(TFDP_STAGE_SORT, s));
         CK(launch_fft_grid(a, advance, s));
         // attraction on the side stream, overlapping sort, spread and FFT
         CK(cudaEventRecord(g->fork_ev, s));
         CK(cudaStreamWaitEvent(g->side_stream, g->fork_ev, 0));
-        if (tm) CK(cudaEventRecordWithFlags(g->ev_attract[0], g->side_stream, cudaEventRecordExternal));
+        CK(begin(TFDP_STAGE_ATTRACT, g->side_stream));
         CK(launch_attract(a, g->side_stream));
-        if (tm) CK(cudaEventRecordWithFlags(g->ev_attract[1], g->side_stream, cudaEventRecordExternal));
+        CK(end(TFDP_STAGE_ATTRACT, g->side_stream));
         CK(cudaEventRecord(g->join_ev, g->side_stream));
         CK(launch_fft_sort(a, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_SORT, s));
+        CK(begin(TFDP_STAGE_SPREAD, s));
         CK(launch_fft_spread(a, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_SPREAD, s));
+        CK(begin(TFDP_STAGE_SPECTRUM, s));
         CK(launch_spectrum(f, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_SPECTRUM, s));
+        CK(begin(TFDP_STAGE_ROWS_FWD, s));
         CK(launch_rows_fwd(f, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_ROWS_FWD, s));
+        CK(begin(TFDP_STAGE_COLS, s));
         CK(launch_cols(f, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_COLS, s));
+        CK(begin(TFDP_STAGE_ROWS_INV, s));
         CK(launch_rows_inv(f, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_ROWS_INV, s));
         CK(cudaStreamWaitEvent(s, g->join_ev, 0));
+        CK(begin(TFDP_STAGE_GATHER_UPDATE, s));
         CK(launch_fft_back(a, advance, eval, s));
-        CK(mark());
+        CK(end(TFDP_STAGE_GATHER_UPDATE, s));
+    }
+    if (tm) {  // the timing branch rejoins the stream at the end of the iteration
+        CK(cudaEventRecord(g->time_join, g->time_stream));
+        CK(cudaStreamWaitEvent(s, g->time_join, 0));
     }
     return TFDP_OK;
 }
@@ -406,7 +432,7 @@ int kernels_per_iteration(const tfdp_graph* g) {
 long long exec_key_of(const tfdp_graph* g) {
     return ((long long)g->params.rep_mode << 40) | ((long long)g->params.k_interp << 32) |
            ((long long)g->dp.gamma_int << 24) | ((long long)g->logP << 16) |
-           ((long long)g->timing << 8) | (long long)(g->fft_mem != nullptr);
+           ((long long)g->timing_mask << 48) | (long long)(g->fft_mem != nullptr);
 }
 
 tfdp_status capture(tfdp_graph* g, int iters, cudaGraphExec_t* out) {
@@ -745,35 +771,43 @@ tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
     return TFDP_OK;
 }
 
-tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable) {
+tfdp_status tfdp_set_stage_timing_mask(tfdp_graph* g, uint32_t mask) {
     if (!g) return TFDP_ERR_INVALID_ARG;
-    if (enable && !g->ev[0]) {
-        for (int i = 0; i <= TFDP_NUM_STAGES; ++i) CK(cudaEventCreate(&g->ev[i]));
-        for (int i = 0; i < 2; ++i) CK(cudaEventCreate(&g->ev_attract[i]));
+    mask &= (1u << TFDP_NUM_STAGES) - 1u;
+    if (mask && !g->ev_b[0]) {
+        for (int i = 0; i < TFDP_NUM_STAGES; ++i) {
+            CK(cudaEventCreate(&g->ev_b[i]));
+            CK(cudaEventCreate(&g->ev_e[i]));
+        }
+        for (int i = 0; i < 2 * TFDP_NUM_STAGES; ++i)
+            CK(cudaEventCreateWithFlags(&g->time_fork[i], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&g->time_join, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&g->time_stream, cudaStreamNonBlocking));
     }
-    if ((bool)enable != g->timing) {
-        g->timing = enable != 0;
-        free_execs(g);  // recapture with / without the event nodes
+    if (mask != g->timing_mask) {
+        g->timing_mask = mask;
+        free_execs(g);  // recapture with the new set of event nodes
     }
     return TFDP_OK;
 }
 
+tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable) {
+    return tfdp_set_stage_timing_mask(g, enable ? (1u << TFDP_NUM_STAGES) - 1u : 0u);
+}
+
 tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages) {
     if (!g || !ms || nstages < 1) return TFDP_ERR_INVALID_ARG;
-    if (!g->timing) return TFDP_ERR_INVALID_ARG;
+    if (!g->timing_mask) return TFDP_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(g->stream));
-    for (int i = 0; i < nstages; ++i) ms[i] = 0.0f;
-    const int used = g->params.rep_mode == TFDP_REP_EXACT ? 2 : 7;
-    const int base = g->params.rep_mode == TFDP_REP_EXACT ? TFDP_STAGE_EXACT : 0;
-    for (int i = 0; i < used; ++i) {
+    const bool exact = g->params.rep_mode == TFDP_REP_EXACT;
+    for (int i = 0; i < nstages; ++i) {
+        ms[i] = 0.0f;
+        if (i >= TFDP_NUM_STAGES || !((g->timing_mask >> i) & 1u)) continue;
+        const bool exact_stage = i == TFDP_STAGE_EXACT || i == TFDP_STAGE_EDGE_UPDATE;
+        if (exact != exact_stage) continue;  // the stage does not run in this mode
         float t = 0.0f;
-        CK(cudaEventElapsedTime(&t, g->ev[i], g->ev[i + 1]));
-        if (base + i < nstages) ms[base + i] = t;
-    }
-    if (g->params.rep_mode != TFDP_REP_EXACT && TFDP_STAGE_ATTRACT < nstages) {
-        float t = 0.0f;
-        CK(cudaEventElapsedTime(&t, g->ev_attract[0], g->ev_attract[1]));
-        ms[TFDP_STAGE_ATTRACT] = t;
+        CK(cudaEventElapsedTime(&t, g->ev_b[i], g->ev_e[i]));
+        ms[i] = t;
     }
     return TFDP_OK;
 }
@@ -821,14 +855,21 @@ tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
     if (!g) return TFDP_OK;
     if (g->stream || g->cap_stream) cudaStreamSynchronize(g->stream);
     free_execs(g);
-    for (int i = 0; i <= TFDP_NUM_STAGES; ++i)
-        if (g->ev[i]) cudaEventDestroy(g->ev[i]);
+    for (int i = 0; i < TFDP_NUM_STAGES; ++i) {
+        if (g->ev_b[i]) cudaEventDestroy(g->ev_b[i]);
+        if (g->ev_e[i]) cudaEventDestroy(g->ev_e[i]);
+    }
+    for (int i = 0; i < 2 * TFDP_NUM_STAGES; ++i)
+        if (g->time_fork[i]) cudaEventDestroy(g->time_fork[i]);
+    if (g->time_join) cudaEventDestroy(g->time_join);
+    if (g->time_stream) {
+        cudaStreamSynchronize(g->time_stream);
+        cudaStreamDestroy(g->time_stream);
+    }
     if (g->fft_mem) cudaFree(g->fft_mem);
     if (g->node_mem) cudaFree(g->node_mem);
     if (g->step_table) cudaFree(g->step_table);
     if (g->side_stream) cudaStreamSynchronize(g->side_stream);
-    for (int i = 0; i < 2; ++i)
-        if (g->ev_attract[i]) cudaEventDestroy(g->ev_attract[i]);
     if (g->fork_ev) cudaEventDestroy(g->fork_ev);
     if (g->join_ev) cudaEventDestroy(g->join_ev);
     if (g->side_stream) cudaStreamDestroy(g->side_stream);

@@ -76,6 +76,7 @@ _SIGS = {
     "tfdp_get_stats": ([_p, ctypes.POINTER(Stats)], ctypes.c_int),
     "tfdp_synchronize": ([_p], ctypes.c_int),
     "tfdp_set_stage_timing": ([_p, ctypes.c_int], ctypes.c_int),
+    "tfdp_set_stage_timing_mask": ([_p, ctypes.c_uint32], ctypes.c_int),
     "tfdp_get_stage_times": ([_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
     "tfdp_destroy_graph": ([_p], ctypes.c_int),
     "tfdp_debug_fetch": ([_p, ctypes.c_int, _p, ctypes.c_size_t], ctypes.c_int),
@@ -242,6 +243,13 @@ class Graph:
 
     def set_stage_timing(self, enable=True):
         _check(lib.tfdp_set_stage_timing(self._h, 1 if enable else 0), "tfdp_set_stage_timing")
+
+    def set_stage_timing_mask(self, stages):
+        """Time only the named stages (an iterable of STAGES names); empty turns it off."""
+        mask = 0
+        for name in stages:
+            mask |= 1 << STAGES.index(name)
+        _check(lib.tfdp_set_stage_timing_mask(self._h, mask), "tfdp_set_stage_timing_mask")
 
     def stage_times(self) -> dict:
         ms = (ctypes.c_float * len(STAGES))()
