@@ -47,6 +47,7 @@ def _lib():
             "or_conv_grid_direct": ([_i64, _d, _d, _i32, _p, _p], None),
             "or_rep_fft": ([_i64, _p, _p, _d, _i32, _d, _d, _i32, _i64, _p], _i32),
             "or_step_size": ([_i64, _i64, _d, _d], _d),
+            "or_k_of_iter": ([_i32, _i64, _i64], _i32),
             "or_update": ([_i64, _p, _p, _d], None),
             "or_iterate": ([_i64, _i64, _p, _p, _d, _d, _d, _i32, _i32, _i32, _i32, _i32, _i64,
                             _d, _d, _i64, _i64, _i64], _i32),
@@ -194,6 +195,12 @@ def step_size(t: int, T: int, s0: float, smin: float) -> float:
     return float(_lib().or_step_size(t, T, s0, smin))
 
 
+def k_of_iter(k: int, t: int, T: int) -> int:
+    """k of iteration t of a T-iteration run; k = 0 is the dynamic strategy of Sec. 3.4
+    "Choices of k" (1 for the first 90 % of the iterations, 2 for the next 5 %, then 3)."""
+    return int(_lib().or_k_of_iter(k, t, T))
+
+
 def update(xy, D, s: float):
     xy = _f64(xy).reshape(-1, 2).copy()
     D = _f64(D).reshape(-1, 2)
@@ -204,7 +211,8 @@ def update(xy, D, s: float):
 def iterate(xy, edges, iters: int, alpha=0.1, beta=8.0, gamma=2.0, mode="exact", k=3,
             n_int_min=50, grid_max=1 << 30, policy=GRID_SNAP_H, P=0, s0=1.0, smin=0.01,
             T=300, t0=0):
-    """Run ``iters`` synchronous t-FDP iterations from iteration index ``t0``."""
+    """Run ``iters`` synchronous t-FDP iterations from iteration index ``t0``; k = 0 takes
+    k per iteration from the dynamic strategy (``k_of_iter``)."""
     xy = _f64(xy).reshape(-1, 2).copy()
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
     m = {"exact": 0, "fft": 1}[mode]

@@ -16,6 +16,9 @@
  *                         interaction by FFT, back-projection, then Eq. (Fr1)/(Fr2)
  *                         with the three kernel sums of Eq. (kernelproduct)
  *   grid size             Sec. 3.4 "Choices of k": N_int = max(50, [L])
+ *   dynamic k             Sec. 3.4 "Choices of k": k = 1 for the first 90% of the
+ *                         iterations, k = 2 for the next 5%, k = 3 for the rest
+ *                         (boundaries floor(0.9 T), floor(0.95 T): a reading)
  *   position update       Sec. 3.1 (move along the resultant force until convergence);
  *                         the step schedule is a reading, the paper gives none.
  *
@@ -446,6 +449,17 @@ static int64_t or_nextpow2(int64_t v) {
     return p;
 }
 
+/* k of iteration t of a T-iteration run (Sec. 3.4 "Choices of k"). k > 0 is fixed;
+ * k = 0 is the paper's dynamic strategy: 1 while t < floor(0.9 T), 2 while
+ * t < floor(0.95 T), then 3 (also for t >= T). With T = 300 that is 270 iterations at
+ * k = 1, the count Sec. 4.2 mentions. */
+int or_k_of_iter(int k, int64_t t, int64_t T) {
+    if (k > 0) return k;
+    if (t < (9 * T) / 10) return 1;
+    if (t < (19 * T) / 20) return 2;
+    return 3;
+}
+
 int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, double alpha, double beta,
                double gamma, int mode, int k, int n_int_min, int grid_max, int policy, int64_t P,
                double s0, double smin, int64_t T, int64_t t0, int64_t iters) {
@@ -459,11 +473,12 @@ int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, double al
             or_rep_exact(n, xy, gamma, 0, n, frep);
         } else {
             for (int64_t i = 0; i < 2 * n; ++i) xyf[i] = (float)xy[i];
+            const int kt = or_k_of_iter(k, t, T);
             double g[5];
-            or_grid_policy(n, xyf, k, n_int_min, grid_max, policy, g);
+            or_grid_policy(n, xyf, kt, n_int_min, grid_max, policy, g);
             int n_int = (int)g[2];
-            int64_t PP = P > 0 ? P : or_nextpow2(2 * (int64_t)n_int * k - 1);
-            rc = or_rep_fft(n, xy, xyf, gamma, k, g[0], g[1], n_int, PP, frep);
+            int64_t PP = P > 0 ? P : or_nextpow2(2 * (int64_t)n_int * kt - 1);
+            rc = or_rep_fft(n, xy, xyf, gamma, kt, g[0], g[1], n_int, PP, frep);
         }
         or_att(n, m, edges, xy, alpha, beta, fatt);
         for (int64_t i = 0; i < 2 * n; ++i) frep[i] += fatt[i];

@@ -345,3 +345,32 @@ def test_ibfft_equals_explicit_interpolated_kernel_matrix(k):
     brute = (Kt.sum(1)[:, None] * xy) - Kt @ xy
     got = oracle.rep_fft(xy, gamma, k, grid={"lo": lo, "h": h, "n_int": n_int})
     np.testing.assert_allclose(got, brute, rtol=1e-10, atol=1e-12)
+
+
+def test_dynamic_k_schedule_counts(paper):
+    """Sec. 3.4 "Choices of k": k = 1 for 90 % of the iterations, 2 for 5 %, 3 for the
+    rest; Sec. 4.2 prints the count of single-point iterations of a 300-iteration run."""
+    d, it = paper["dynamic_k"], paper["dynamic_k_iterations"]
+    T = it["T"]
+    ks = [oracle.k_of_iter(0, t, T) for t in range(T)]
+    assert ks.count(1) == it["k1_iterations"]
+    counts = [ks.count(k) for k in d["k"]]
+    assert counts == [round(f * T) for f in d["fractions"]]
+    assert ks == sorted(ks)                      # 1s, then 2s, then 3s
+    assert oracle.k_of_iter(0, T + 5, T) == 3    # past the schedule: the last k
+    assert all(oracle.k_of_iter(k, t, T) == k for k in (1, 2, 3) for t in (0, T - 1))
+
+
+def test_dynamic_k_iteration_is_the_fixed_k_segments():
+    """A dynamic-k run equals fixed-k runs chained at the schedule's boundaries (T = 20:
+    k = 1 for t < 18, k = 2 at t = 18, k = 3 at t = 19)."""
+    e, xy = _random_graph(60, 150, 7)
+    xy = xy * 6.0
+    kw = dict(mode="fft", n_int_min=4, grid_max=30, T=20, alpha=0.1, beta=8.0, gamma=2.0)
+    dyn = oracle.iterate(xy, e, 20, k=0, **kw)
+    x = oracle.iterate(xy, e, 18, k=1, t0=0, **kw)
+    x = oracle.iterate(x, e, 1, k=2, t0=18, **kw)
+    x = oracle.iterate(x, e, 1, k=3, t0=19, **kw)
+    assert np.array_equal(dyn, x)
+    # and differs from a fixed-k run, so the switch is not a no-op
+    assert not np.array_equal(dyn, oracle.iterate(xy, e, 20, k=3, **kw))
