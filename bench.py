@@ -345,6 +345,39 @@ def serving_measurement(jobs=200, rate=20.0, updates=5, init_iters=300, upd_iter
             "chunk_iters": chunk}
 
 
+def dynamic_k_measurement(e, xy, spec, stream, sampler=None):
+    """One whole layout (total_iters iterations) of the same graph with the dynamic k
+    schedule of Sec. 3.4 (k = 1 for 90 % of the iterations, then 2, then 3) against the
+    fixed k = 3 of the main line. Each run starts from the same positions, after one
+    untimed run that captures the iteration graphs of every k."""
+    import torch
+    from paper_2303_03964_gb300 import tfdp
+    n, T = xy.shape[0], spec["total_iters"]
+    out = {"workload": "%d-iteration layout from X0 of the same workload, CUDA events around "
+                       "the whole layout" % T}
+    for name, k in (("fixed_k3", 3), ("dynamic", tfdp.K_DYNAMIC)):
+        p = tfdp.params_default(k_interp=k, grid_max=spec["grid_max"], total_iters=T)
+        with tfdp.Graph(n, e, xy, p, stream=stream.cuda_stream) as g:
+            g.iterate(T)
+            g.set_positions(xy)
+            g.set_iteration(0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            if sampler is not None:
+                sampler.active = True
+            e0.record(stream)
+            g.iterate(T)
+            e1.record(stream)
+            stream.synchronize()
+            if sampler is not None and isinstance(sampler, NvmlSampler):
+                sampler.active = False
+            ms = e0.elapsed_time(e1)
+            flags = g.stats()["device_flags"]
+        out[name] = {"layout_ms": ms, "value": n * T / (ms * 1e-3), "unit": UNIT, "device_flags": flags}
+    out["speedup"] = out["fixed_k3"]["layout_ms"] / out["dynamic"]["layout_ms"]
+    return out
+
+
 def cpu_baseline(e, xy, spec, budget_s=15.0):
     """The FP64 oracle as it stands, on the same workload, on this host's cores."""
     import numpy as np
@@ -574,6 +607,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and args.workload == "lattice_1m":
         serving = serving_measurement(sampler=sampler)
+    dynamic_k = None
+    if not args.no_dynamic_k and spec["rep"] == "fft":
+        dynamic_k = dynamic_k_measurement(e, xy, spec, stream, sampler=sampler)
     clocks = sampler.stop()
     value = ws * n * args.steps / (total_ms * 1e-3)
     q = sorted(step_ms)
@@ -590,6 +626,7 @@ def run_ours(args):
         "mixed": None,
         "batched": batched,
         "serving": serving,
+        "dynamic_k": dynamic_k,
         "stages_ms": mean_stage,
         "stages_note": "5 steps after the timed region with every stage bracketed by events "
                        "(the timed steps bracket only the roofline kernel)",
@@ -618,6 +655,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-dynamic-k", action="store_true",
+                    help="skip the whole-layout comparison of the dynamic k schedule with k = 3")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -73,11 +73,17 @@ typedef enum {
                             rebuilt only when h crosses a 1/16-octave step */
 } tfdp_grid_policy;
 
+#define TFDP_K_DYNAMIC 0
+
 typedef struct {
     double alpha;        /* attraction weight (Sec. 3.3), default 0.1, >= 0 */
     double beta;         /* short-range attraction weight (Sec. 3.3), default 8, >= 0 */
     double gamma;        /* repulsion exponent (Sec. 3.3), default 2, > 1 (Eq. exponentcondiction) */
-    int32_t k_interp;    /* interpolation nodes per box and axis, 1..3, default 3 (Sec. 3.4) */
+    int32_t k_interp;    /* interpolation nodes per box and axis, 1..3, default 3 (Sec. 3.4);
+                          * TFDP_K_DYNAMIC (0): the paper's dynamic strategy (Sec. 3.4 "Choices
+                          * of k"): k = 1 while t < floor(0.9 T), 2 while t < floor(0.95 T),
+                          * then 3, with T = total_iters (FFT path; the boundaries are a
+                          * reading). Buffers are sized for the largest need over k = 1..3. */
     int32_t n_int_min;   /* lower bound of N_int, default 50 (Sec. 3.4) */
     int32_t grid_max;    /* cap on G = N_int * k, default 1023; sizes the FFT: P = nextpow2(2 grid_max - 1) */
     int32_t grid_policy; /* tfdp_grid_policy, default TFDP_GRID_SNAP_H */
@@ -101,7 +107,8 @@ typedef struct {
     int32_t spectrum_builds;  /* how many times the kernel spectrum was (re)built */
     int32_t device_flags;     /* nonzero: a device-side check failed (bit field) */
     int32_t kernels_per_iteration; /* kernel launches of one iteration in the current mode */
-    int32_t reserved[6];
+    int32_t grid_k;           /* interpolation nodes per box and axis of that iteration */
+    int32_t reserved[5];
 } tfdp_stats;
 
 /* Stages of one iteration, in launch order, for tfdp_get_stage_times. */
@@ -229,7 +236,8 @@ typedef struct tfdp_batch tfdp_batch;
  *   edges      per graph host pointer to 2 m int32 ids (NULL allowed when m = 0)
  *   xy0        per graph host pointer to n x 2 FP32 initial positions
  *   params     NULL (defaults for all) or num_graphs parameter sets; rep_mode is forced
- *              to TFDP_REP_FFT; all graphs must share k_interp. The FFT size is the
+ *              to TFDP_REP_FFT; all graphs must share one fixed k_interp (1..3;
+ *              TFDP_K_DYNAMIC gives TFDP_ERR_PARAM_RANGE). The FFT size is the
  *              largest any graph needs and must be <= 2048 (grid_max <= 1024), else
  *              TFDP_ERR_PARAM_RANGE.
  *   stream     cudaStream_t for all work of the batch

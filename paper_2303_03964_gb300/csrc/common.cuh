@@ -28,7 +28,7 @@ enum : unsigned {
 struct DevParams {
     double alpha, beta, gamma;
     double step0, step_min;
-    int k;
+    int k;           // interpolation nodes per box and axis; 0 = dynamic (k_of_iter)
     int n_int_min;
     int grid_max;
     int policy;
@@ -51,7 +51,19 @@ struct GridDesc {
     float hk_f;     // h / k rounded to FP32 (grid spacing)
     int n_int;
     int G;
+    int k;          // interpolation nodes per box and axis in this iteration
 };
+
+// k of iteration t of a T-iteration run (Sec. 3.4 "Choices of k"). k > 0 is fixed;
+// k = 0 is the paper's dynamic strategy: 1 while t < floor(0.9 T), 2 while
+// t < floor(0.95 T), then 3 (the boundaries are a reading). The host picks the
+// iteration graph of each segment with the same function.
+__host__ __device__ __forceinline__ int k_of_iter(int k, long long t, long long T) {
+    if (k > 0) return k;
+    if (t < (9 * T) / 10) return 1;
+    if (t < (19 * T) / 20) return 2;
+    return 3;
+}
 
 // Mutable state of one graph on the device.
 struct DevState {
@@ -91,14 +103,14 @@ constexpr unsigned kOrdMaxInit = 0u;           // identity of atomicMax
 // Sec. 3.4 "Choices of k": N_int = max(n_int_min, ceil(L)), capped at floor(grid_max/k).
 // All decisions are exact FP64 operations on FP32 extremes, so the CPU oracle, which
 // performs the same operations, obtains the same N_int and h.
-__device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevParams& p) {
+__device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevParams& p, int k) {
     GridDesc g;
     double L = (double)hi_f - (double)lo_f;
     if (!(L >= kLFloor)) L = kLFloor;  // also catches NaN
     double c = ceil(L);
     if (c > 2.0e9) c = 2.0e9;
     int n_int = (c > (double)p.n_int_min) ? (int)c : p.n_int_min;
-    int cap = p.grid_max / p.k;
+    int cap = p.grid_max / k;
     if (n_int > cap) n_int = cap;
     if (n_int < 1) n_int = 1;
     double h;
@@ -121,9 +133,10 @@ __device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevP
     g.lo_f = lo_f;
     g.h_f = __double2float_rn(h);
     g.h_lo_f = __double2float_rn(h - (double)g.h_f);
-    g.hk_f = __double2float_rn(h / (double)p.k);
+    g.hk_f = __double2float_rn(h / (double)k);
     g.n_int = n_int;
-    g.G = n_int * p.k;
+    g.G = n_int * k;
+    g.k = k;
     return g;
 }
 

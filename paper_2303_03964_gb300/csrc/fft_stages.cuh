@@ -41,7 +41,7 @@ struct KernelSource {
     float s2, s, gamma;  // spacing^2, spacing, exponent (FP32)
     int gamma_int;
     __device__ __forceinline__ void bind(const DevState* st, const DevParams* prm) {
-        const double sd = st->grid.h / (double)prm->k;
+        const double sd = st->grid.h / (double)st->grid.k;
         s = (float)sd;
         s2 = (float)(sd * sd);
         gamma = (float)prm->gamma;

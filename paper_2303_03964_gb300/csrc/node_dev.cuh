@@ -108,7 +108,8 @@ __device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, 
     const unsigned b00 = st->bbox[0][0], b01 = st->bbox[0][1], b10 = st->bbox[1][0], b11 = st->bbox[1][1];
     const long long t = st->iter;
     const int cur = (int)(t & 1);
-    const GridDesc g = make_grid(ord2f(cur ? b10 : b00), ord2f(cur ? b11 : b01), prm);
+    const int kt = k_of_iter(prm.k, t, prm.total_iters);
+    const GridDesc g = make_grid(ord2f(cur ? b10 : b00), ord2f(cur ? b11 : b01), prm, kt);
     st->grid = g;
     st->t_cur = t;
     if (with_step) st->step_cur = step_size(t, prm);
@@ -119,12 +120,12 @@ __device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, 
         st->bbox[cur ^ 1][1] = kOrdMaxInit;
     }
     const bool valid = st->spec_valid && st->spec_h == g.h && st->spec_gamma == prm.gamma &&
-                       st->spec_k == prm.k && st->spec_P == prm.P;
+                       st->spec_k == kt && st->spec_P == prm.P;
     st->spec_dirty = valid ? 0 : 1;
     if (!valid) {
         st->spec_h = g.h;
         st->spec_gamma = prm.gamma;
-        st->spec_k = prm.k;
+        st->spec_k = kt;
         st->spec_P = prm.P;
         st->spec_valid = 1;
         st->spec_builds += 1;

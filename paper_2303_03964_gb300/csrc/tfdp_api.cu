@@ -116,8 +116,9 @@ struct tfdp_graph {
     float2* tw = nullptr;
 
     // captured iterations
-    cudaGraphExec_t exec1 = nullptr, execB = nullptr;
-    long long exec_key = -1;
+    // captured iterations, one pair (1 and kBatchIters iterations) per k
+    cudaGraphExec_t exec1[kMaxK + 1] = {}, execB[kMaxK + 1] = {};
+    long long exec_key[kMaxK + 1] = {-1, -1, -1, -1};
 
     // stage timing: begin / end events around the stages whose bit is set in timing_mask
     unsigned timing_mask = 0;
@@ -132,10 +133,13 @@ struct tfdp_graph {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
-    NodeLaunch node_launch() const {
+    // k of the next iteration (the fixed k, or the dynamic schedule's k at host_iter)
+    int k_now() const { return k_of_iter(params.k_interp, host_iter, params.total_iters); }
+
+    NodeLaunch node_launch(int k = 0) const {
         NodeLaunch a{};
         a.n = (int)n;
-        a.k = params.k_interp;
+        a.k = k ? k : k_now();
         a.gamma_int = dp.gamma_int;
         a.xy[0] = xy[0];
         a.xy[1] = xy[1];
@@ -204,11 +208,14 @@ DevParams make_dev_params(const tfdp_params& p, int P, int logP) {
     return d;
 }
 
-// FFT geometry implied by the parameters.
+// FFT geometry implied by the parameters: the largest grid and box count over the k
+// the graph can use (all of 1..3 under the dynamic schedule; k = 1 has the most boxes).
 bool fft_geometry(const tfdp_params& p, int* P, int* logP, int* G_max, int* nbox_max) {
-    const int n_int_max = p.grid_max / p.k_interp;
-    if (n_int_max < 1) return false;
-    const int G = n_int_max * p.k_interp;
+    const int k_lo = p.k_interp ? p.k_interp : 1, k_hi = p.k_interp ? p.k_interp : kMaxK;
+    const int n_int_max = p.grid_max / k_lo;
+    if (p.grid_max / k_hi < 1) return false;
+    int G = 0;
+    for (int k = k_lo; k <= k_hi; ++k) G = std::max(G, (p.grid_max / k) * k);
     int l = log2_ceil(2LL * G - 1);
     if (l < kMinLogP) l = kMinLogP;
     if (l > kMaxLogP) return false;
@@ -220,10 +227,12 @@ bool fft_geometry(const tfdp_params& p, int* P, int* logP, int* G_max, int* nbox
 }
 
 void free_execs(tfdp_graph* g) {
-    if (g->exec1) cudaGraphExecDestroy(g->exec1);
-    if (g->execB) cudaGraphExecDestroy(g->execB);
-    g->exec1 = g->execB = nullptr;
-    g->exec_key = -1;
+    for (int k = 0; k <= kMaxK; ++k) {
+        if (g->exec1[k]) cudaGraphExecDestroy(g->exec1[k]);
+        if (g->execB[k]) cudaGraphExecDestroy(g->execB[k]);
+        g->exec1[k] = g->execB[k] = nullptr;
+        g->exec_key[k] = -1;
+    }
 }
 
 tfdp_status alloc_fft(tfdp_graph* g) {
@@ -357,8 +366,8 @@ tfdp_status refresh_bbox(tfdp_graph* g) {
 // a branch of their own (forked from the stage's stream at each border, joined at the
 // end), so no kernel waits for one; inside a captured graph they become event-record
 // nodes off the kernel chain.
-tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval) {
-    const NodeLaunch a = g->node_launch();
+tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval, int k) {
+    const NodeLaunch a = g->node_launch(k);
     const unsigned tm = g->timing_mask;
     // cudaEventRecordExternal makes the record a node of a captured graph (a plain
     // record inside a capture only orders the capture and is never timed)
@@ -429,17 +438,18 @@ int kernels_per_iteration(const tfdp_graph* g) {
     return (1 + 4 + 1 + 1 + 1 + 1 + 1) + (g->logP > 12 ? 2 : 0);
 }
 
-long long exec_key_of(const tfdp_graph* g) {
-    return ((long long)g->params.rep_mode << 40) | ((long long)g->params.k_interp << 32) |
+long long exec_key_of(const tfdp_graph* g, int k) {
+    return ((long long)g->params.rep_mode << 40) | ((long long)k << 32) |
            ((long long)g->dp.gamma_int << 24) | ((long long)g->logP << 16) |
            ((long long)g->timing_mask << 48) | (long long)(g->fft_mem != nullptr);
 }
 
-tfdp_status capture(tfdp_graph* g, int iters, cudaGraphExec_t* out) {
+// Capture `iters` iterations with the kernels of interpolation order k.
+tfdp_status capture(tfdp_graph* g, int iters, int k, cudaGraphExec_t* out) {
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeThreadLocal));
     tfdp_status st = TFDP_OK;
-    for (int i = 0; i < iters && st == TFDP_OK; ++i) st = enqueue_step(g, g->cap_stream, 1, 0);
+    for (int i = 0; i < iters && st == TFDP_OK; ++i) st = enqueue_step(g, g->cap_stream, 1, 0, k);
     cudaError_t e = cudaStreamEndCapture(g->cap_stream, &graph);
     if (st != TFDP_OK) {
         if (graph) cudaGraphDestroy(graph);
@@ -452,15 +462,18 @@ tfdp_status capture(tfdp_graph* g, int iters, cudaGraphExec_t* out) {
     return TFDP_OK;
 }
 
-tfdp_status ensure_execs(tfdp_graph* g) {
-    const long long key = exec_key_of(g);
-    if (g->exec1 && g->execB && g->exec_key == key) return TFDP_OK;
-    free_execs(g);
-    tfdp_status st = capture(g, 1, &g->exec1);
+tfdp_status ensure_execs(tfdp_graph* g, int k) {
+    const long long key = exec_key_of(g, k);
+    if (g->exec1[k] && g->execB[k] && g->exec_key[k] == key) return TFDP_OK;
+    if (g->exec1[k]) cudaGraphExecDestroy(g->exec1[k]);
+    if (g->execB[k]) cudaGraphExecDestroy(g->execB[k]);
+    g->exec1[k] = g->execB[k] = nullptr;
+    g->exec_key[k] = -1;
+    tfdp_status st = capture(g, 1, k, &g->exec1[k]);
     if (st != TFDP_OK) return st;
-    st = capture(g, kBatchIters, &g->execB);
+    st = capture(g, kBatchIters, k, &g->execB[k]);
     if (st != TFDP_OK) return st;
-    g->exec_key = key;
+    g->exec_key[k] = key;
     return TFDP_OK;
 }
 
@@ -515,9 +528,9 @@ tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
     if (!(p->gamma > 1.0) || !std::isfinite(p->gamma)) return TFDP_ERR_PARAM_RANGE;
     if (!(p->alpha >= 0.0) || !std::isfinite(p->alpha)) return TFDP_ERR_PARAM_RANGE;
     if (!(p->beta >= 0.0) || !std::isfinite(p->beta)) return TFDP_ERR_PARAM_RANGE;
-    if (p->k_interp < 1 || p->k_interp > kMaxK) return TFDP_ERR_PARAM_RANGE;
+    if (p->k_interp < 0 || p->k_interp > kMaxK) return TFDP_ERR_PARAM_RANGE;  // 0: dynamic
     if (p->n_int_min < 1) return TFDP_ERR_PARAM_RANGE;
-    if (p->grid_max < p->k_interp) return TFDP_ERR_PARAM_RANGE;
+    if (p->grid_max < (p->k_interp ? p->k_interp : kMaxK)) return TFDP_ERR_PARAM_RANGE;
     if (p->grid_policy != TFDP_GRID_PAPER && p->grid_policy != TFDP_GRID_SNAP_H) return TFDP_ERR_INVALID_ARG;
     if (p->rep_mode != TFDP_REP_EXACT && p->rep_mode != TFDP_REP_FFT) return TFDP_ERR_INVALID_ARG;
     if (p->precision != TFDP_PREC_FP32) return TFDP_ERR_PARAM_RANGE;  // BF16X3: not built
@@ -711,15 +724,24 @@ tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
         g->host_iter += iters;
         return tfdp_set_iteration(g, g->host_iter);
     }
-    tfdp_status st = ensure_execs(g);
-    if (st != TFDP_OK) return st;
+    // segments of constant k (one segment unless the dynamic schedule switches k); the
+    // device derives the same k from its iteration counter
     int left = iters;
-    while (left >= kBatchIters) {
-        CK(cudaGraphLaunch(g->execB, g->stream));
-        left -= kBatchIters;
+    while (left > 0) {
+        const int k = g->k_now();
+        int seg = 0;
+        while (seg < left && k_of_iter(g->params.k_interp, g->host_iter + seg, g->params.total_iters) == k) ++seg;
+        tfdp_status st = ensure_execs(g, k);
+        if (st != TFDP_OK) return st;
+        int todo = seg;
+        while (todo >= kBatchIters) {
+            CK(cudaGraphLaunch(g->execB[k], g->stream));
+            todo -= kBatchIters;
+        }
+        while (todo-- > 0) CK(cudaGraphLaunch(g->exec1[k], g->stream));
+        g->host_iter += seg;
+        left -= seg;
     }
-    while (left-- > 0) CK(cudaGraphLaunch(g->exec1, g->stream));
-    g->host_iter += iters;
     g->last_was_eval = false;
     return TFDP_OK;
 }
@@ -741,7 +763,7 @@ tfdp_status tfdp_set_iteration(tfdp_graph* g, int64_t t) {
 tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_device) {
     if (!g) return TFDP_ERR_INVALID_ARG;
     if (g->n == 0) return TFDP_OK;
-    tfdp_status st = enqueue_step(g, g->stream, 0, 1);
+    tfdp_status st = enqueue_step(g, g->stream, 0, 1, g->k_now());
     if (st != TFDP_OK) return st;
     g->last_was_eval = true;
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -768,6 +790,7 @@ tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
     out->spectrum_builds = s.spec_builds;
     out->device_flags = (int32_t)s.flags;
     out->kernels_per_iteration = kernels_per_iteration(g);
+    out->grid_k = s.grid.k;
     return TFDP_OK;
 }
 

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libtfdp.so")
 REP_EXACT, REP_FFT = 0, 1
 PREC_FP32, PREC_BF16X3 = 0, 1
 GRID_PAPER, GRID_SNAP_H = 0, 1
+K_DYNAMIC = 0  # k_interp: the dynamic k schedule (1, then 2, then 3)
 DEBUG_GRID_CHARGES, DEBUG_GRID_OUTPUT, DEBUG_SORT_PERM, DEBUG_CELL_START = 1, 2, 3, 4
 STAGES = ["sort", "spread", "spectrum", "rows_fwd", "cols", "rows_inv", "gather_update",
           "exact", "edge_update", "attract"]
@@ -50,7 +51,7 @@ class Stats(ctypes.Structure):
                 ("grid_n_int", ctypes.c_int32), ("grid_G", ctypes.c_int32),
                 ("fft_P", ctypes.c_int32), ("spectrum_builds", ctypes.c_int32),
                 ("device_flags", ctypes.c_int32), ("kernels_per_iteration", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("grid_k", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -42,7 +42,7 @@ def test_params_default_values_are_the_papers():
 
 @pytest.mark.parametrize("field,value,status", [
     ("gamma", 1.0, 3), ("gamma", 0.5, 3), ("alpha", -0.1, 3), ("beta", -1.0, 3),
-    ("k_interp", 0, 3), ("k_interp", 4, 3), ("grid_max", 2, 3), ("total_iters", 0, 3),
+    ("k_interp", -1, 3), ("k_interp", 4, 3), ("grid_max", 2, 3), ("total_iters", 0, 3),
     ("step_min", 0.0, 3), ("grid_policy", 7, 1), ("rep_mode", 5, 1), ("grid_max", 1 << 20, 3),
 ])
 def test_params_range_rejected(field, value, status):
@@ -50,6 +50,21 @@ def test_params_range_rejected(field, value, status):
     with pytest.raises(tfdp.TfdpError) as ei:
         tfdp.params_check(p)
     assert ei.value.status == status
+
+
+def test_dynamic_k_accepted_and_sized_for_every_k():
+    # Sec. 3.4 "Choices of k": k_interp = 0 runs k = 1, 2, 3 in turn, so the buffers
+    # must hold k = 1's N_int^2 boxes (grid_max^2) and the largest G over the three
+    p = tfdp.params_default(k_interp=tfdp.K_DYNAMIC, grid_max=1023)
+    assert tfdp.params_check(p) is True
+    dyn = tfdp.graph_footprint(100_000, 200_000, p)
+    k1 = tfdp.graph_footprint(100_000, 200_000, tfdp.params_default(k_interp=1, grid_max=1023))
+    k3 = tfdp.graph_footprint(100_000, 200_000, tfdp.params_default(k_interp=3, grid_max=1023))
+    assert dyn >= max(k1, k3)
+    # the dynamic schedule needs room for k = 3 boxes: grid_max >= 3
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.params_check(tfdp.params_default(k_interp=tfdp.K_DYNAMIC, grid_max=2))
+    assert ei.value.status == 3
 
 
 def test_soft_weight_condition_is_flagged_not_rejected():

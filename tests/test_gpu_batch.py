@@ -89,3 +89,7 @@ def test_batch_rejects_mixed_k_and_bad_graph(tfdp):
     with pytest.raises(tfdp.TfdpError) as ei:
         tfdp.Batch([g1, bad])
     assert ei.value.status == 2
+    # one fixed k per batch: the dynamic schedule is for single graphs
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.Batch([g1, g1], [tfdp.params_default(k_interp=tfdp.K_DYNAMIC)] * 2)
+    assert ei.value.status == 3

@@ -344,3 +344,47 @@ def test_set_positions_and_iteration_counter(tfdp):
         g.set_iteration(7)
         g.iterate(3)
         assert rel_l2(g.get_positions(), c) < 1e-6
+
+
+# ------------------------------------------------------------------ dynamic k (Sec. 3.4)
+
+def _sbm20k(seed):
+    rng = np.random.default_rng(seed)
+    n = 20000
+    e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
+    xy = rng.uniform(-70, 70, size=(n, 2)).astype(np.float32)
+    return n, e, xy
+
+
+def test_dynamic_k_layout_matches_oracle(tfdp):
+    """k_interp = 0 over a 20-iteration schedule: k = 1 for t < 18, 2 at t = 18, 3 at
+    t = 19 (Sec. 3.4 "Choices of k"); positions after all three phases against the
+    oracle's dynamic-k run."""
+    n, e, xy = _sbm20k(21)
+    T = 20
+    p = _params(tfdp, k_interp=tfdp.K_DYNAMIC, grid_max=255, total_iters=T)
+    with tfdp.Graph(n, e, xy, p) as g:
+        g.iterate(7)
+        g.iterate(T - 7)  # a call that crosses both switches
+        out = g.get_positions()
+        st = g.stats()
+    assert st["device_flags"] == 0 and st["iteration"] == T
+    assert st["grid_k"] == 3 and st["spectrum_builds"] >= 3
+    ref = oracle.iterate(xy.astype(np.float64), e, T, mode="fft", k=0, grid_max=255,
+                         policy=oracle.GRID_SNAP_H, P=st["fft_P"], T=T)
+    assert record("fft_dynk_sbm20k_20it_pos", rel_l2(out, ref)) <= POS_TOL
+
+
+@pytest.mark.parametrize("t", [0, 18, 19])
+def test_dynamic_k_forces_in_each_phase(tfdp, t):
+    n, e, xy = _sbm20k(22)
+    T = 20
+    p = _params(tfdp, k_interp=tfdp.K_DYNAMIC, grid_max=255, total_iters=T)
+    with tfdp.Graph(n, e, xy, p) as g:
+        g.set_iteration(t)
+        fr, _ = g.eval_forces()
+        st = g.stats()
+    k = oracle.k_of_iter(0, t, T)
+    assert st["grid_k"] == k
+    _, ref = _oracle_fft(xy, st, 2.0, k, 255, 1)
+    assert record("fft_dynk_forces_t%d_k%d" % (t, k), rel_l2(fr, ref)) <= FORCE_TOL
