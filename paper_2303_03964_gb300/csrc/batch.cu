@@ -59,7 +59,6 @@ struct BatchArgs {
     float2* xy[2];          // packed caller-order positions (global node index)
     float2* vxy[2];         // packed visit orders (see launch.h NodeLaunch)
     int* vperm[2];          // global node ids
-    int* rank;              // global sorted slot of each node
     int2* keyslot;
     float2* fatt;
     float2* frep;
@@ -199,7 +198,6 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
                 } else {
                     a.vxy[cur ^ 1][G.node_off + pos] = a.vxy[cur][gv];
                     a.vperm[cur ^ 1][G.node_off + pos] = i;
-                    a.rank[i] = G.node_off + pos;
                 }
             }
         }
@@ -644,7 +642,7 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
     const size_t o_xy0 = take(sizeof(float2) * N), o_xy1 = take(sizeof(float2) * N);
     const size_t o_vx0 = take(sizeof(float2) * N), o_vx1 = take(sizeof(float2) * N);
     const size_t o_vp0 = take(sizeof(int) * N), o_vp1 = take(sizeof(int) * N);
-    const size_t o_rank = take(sizeof(int) * N), o_ks = take(sizeof(int2) * N);
+    const size_t o_ks = take(sizeof(int2) * N);
     const size_t o_fatt = take(sizeof(float2) * N), o_frep = take(sizeof(float2) * N);
     const size_t o_rp = take(sizeof(int) * rowptr.size()), o_col = take(sizeof(int) * std::max<size_t>(col.size(), 1));
     const size_t o_tw = take(sizeof(float2) * b->P);
@@ -668,7 +666,6 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
     a.vxy[1] = (float2*)(base + o_vx1);
     a.vperm[0] = (int*)(base + o_vp0);
     a.vperm[1] = (int*)(base + o_vp1);
-    a.rank = (int*)(base + o_rank);
     a.keyslot = (int2*)(base + o_ks);
     a.fatt = (float2*)(base + o_fatt);
     a.frep = (float2*)(base + o_frep);

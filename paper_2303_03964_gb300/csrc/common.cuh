@@ -8,7 +8,35 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace tfdp {
+
+// ---------------------------------------------------------------- dependent launch
+// Kernels of one iteration run back to back on one stream. Launched with
+// launch_pdl, a kernel may be scheduled while its predecessor is still finishing; it
+// calls pdl_wait() first, which returns once the predecessor grid has completed and its
+// writes are visible (a no-op when the launch had no programmatic predecessor), and
+// pdl_trigger() to let its own successor be scheduled early. Only kernels that start
+// with pdl_wait() are launched this way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 constexpr int kMaxK = 3;
 constexpr double kLFloor = 1.0 / 1024.0;  // narrowest layout square side

@@ -225,6 +225,8 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<
     k_rows_fwd_r(GridSource gsrc, int data_blocks, float2* __restrict__ T1, int ystride, float2* __restrict__ S1,
                  const float2* __restrict__ tw, const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     if ((int)blockIdx.x < data_blocks) {
         rows_fwd_body<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
     } else {
@@ -242,6 +244,8 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<
              float* __restrict__ specHx, float* __restrict__ specHy, const float2* __restrict__ S1,
              const float2* __restrict__ tw, const DevState* __restrict__ st) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     cols_body<LOGP>(blockIdx.x, T1, T2, ystride, specK, specHx, specHy, S1, tw, st->grid.G, st->spec_dirty, sm);
 }
 
@@ -250,6 +254,8 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<
     k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
                  const float2* __restrict__ tw, const DevState* __restrict__ st) {
     extern __shared__ float2 sm[];
+    pdl_wait();
+    pdl_trigger();
     rows_inv_body<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
 }
 
@@ -337,9 +343,8 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
         using Rg = RegGeom<L>;
         const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
         const int spec_blocks = Rg::P / (2 * Rg::RG);
-        k_rows_fwd_r<L><<<blocks + spec_blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(gs, blocks, a.T1, a.ystride, a.S1,
-                                                                                  a.tw, a.st, a.prm);
-        return cudaGetLastError();
+        return launch_pdl(k_rows_fwd_r<L>, blocks + spec_blocks, Rg::T * Rg::RG, Rg::rows_smem, s, gs, blocks, a.T1,
+                          a.ystride, a.S1, a.tw, (const DevState*)a.st, (const DevParams*)a.prm);
     }
     const int row_blocks = (a.G_max + Gm::RPC - 1) / Gm::RPC;
     k_rows_fwd<LOGP, Gm::RPC, GridSource><<<row_blocks, 256, Gm::rows_smem, s>>>(gs, a.T1, a.ystride, a.tw, a.st, a.prm);
@@ -356,9 +361,9 @@ static cudaError_t launch_cols_impl(const FftLaunch& a, cudaStream_t s) {
         constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
         using Rg = RegGeom<L>;
         const int blocks = (P / 2 + 1 + Rg::CG - 1) / Rg::CG;
-        k_cols_r<L><<<blocks, Rg::T * Rg::CG, Rg::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy,
-                                                                   a.S1, a.tw, a.st);
-        return cudaGetLastError();
+        return launch_pdl(k_cols_r<L>, blocks, Rg::T * Rg::CG, Rg::cols_smem, s, (const float2*)a.T1, a.T2,
+                          a.ystride, a.specK, a.specHx, a.specHy, (const float2*)a.S1, (const float2*)a.tw,
+                          (const DevState*)a.st);
     }
     k_cols<LOGP><<<P / 2 + 1, 256, Gm::cols_smem, s>>>(a.T1, a.T2, a.ystride, a.specK, a.specHx, a.specHy, a.tw, a.st);
     return cudaGetLastError();
@@ -373,8 +378,8 @@ static cudaError_t launch_rows_inv_impl(const FftLaunch& a, cudaStream_t s) {
         constexpr int L = (LOGP <= kMaxRegLogP ? LOGP : kMaxRegLogP);
         using Rg = RegGeom<L>;
         const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-        k_rows_inv_r<L><<<blocks, Rg::T * Rg::RG, Rg::rows_smem, s>>>(a.T2, a.ystride, a.gout, a.Gs, a.tw, a.st);
-        return cudaGetLastError();
+        return launch_pdl(k_rows_inv_r<L>, blocks, Rg::T * Rg::RG, Rg::rows_smem, s, (const float2*)a.T2, a.ystride,
+                          a.gout, a.Gs, (const float2*)a.tw, (const DevState*)a.st);
     }
     const int row_blocks = (a.G_max + Gm::RPC - 1) / Gm::RPC;
     k_rows_inv<LOGP, Gm::RPC><<<row_blocks, 256, Gm::rows_smem, s>>>(a.T2, a.ystride, a.gout, a.Gs, a.tw, a.st);

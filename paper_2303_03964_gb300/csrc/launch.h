@@ -56,10 +56,9 @@ struct NodeLaunch {
     // Visit orders: iteration t visits nodes in order vperm[t & 1] (the cell-sorted order
     // of iteration t - 1) with positions vxy[t & 1]; its sort writes the new order into
     // vperm[t & 1 ^ 1] / vxy[t & 1 ^ 1] (old positions, which the update then overwrites
-    // with the new ones), and rank[i] = slot of node i in the new order.
+    // with the new ones).
     int* vperm[2];         // n each
     float2* vxy[2];        // n each
-    int* rank;             // n
     float* gin;            // spread output
     int Gs;
     const float4* gout;    // grid output

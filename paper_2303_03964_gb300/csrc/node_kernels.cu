@@ -107,6 +107,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict_
 // Lane 1 fetches s_t from the step table while lane 0 decides the grid, so the table's
 // dependent load overlaps the FP64 work.
 __global__ void k_grid(NodeLaunch a, int advance) {
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 1) {
         a.st->step_cur = step_size(a.st->iter, *a.prm);
         return;
@@ -120,6 +122,8 @@ __global__ void k_grid(NodeLaunch a, int advance) {
 // histogram), visiting nodes in the previous iteration's cell-sorted order: neighbouring
 // lanes mostly share a box, so one atomic serves all lanes of a warp with that box.
 __global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a) {
+    pdl_wait();
+    pdl_trigger();
     const DevState* st = a.st;
     const int cur = (int)(st->t_cur & 1);
     const float2* __restrict__ vxy = a.vxy[cur];
@@ -163,6 +167,8 @@ constexpr int kLookbackSpinLimit = 1 << 20;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, int ntiles,
                                                                  unsigned long long* __restrict__ status) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ unsigned long long s_ticket;
     __shared__ int s_w[32];
     __shared__ int s_prefix;
@@ -282,6 +288,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
 
 // ---------------------------------------------------------------- FFT path: scatter
 __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
+    pdl_wait();
+    pdl_trigger();
     const int cur = (int)(a.st->t_cur & 1);
     const int* __restrict__ vperm = a.vperm[cur];
     const float2* __restrict__ vxy = a.vxy[cur];
@@ -301,7 +309,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
         }
         nxy[pos] = vxy[v];
         nperm[pos] = i;
-        a.rank[i] = pos;
     }
 }
 
@@ -310,6 +317,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
 // Lagrange weights w (rho) and of w times the offset to each grid node (m^x, m^y).
 template <int K>
 __global__ void __launch_bounds__(kNodeThreads, 3) k_spread(NodeLaunch a) {
+    pdl_wait();
+    pdl_trigger();
     const GridDesc g = a.st->grid;
     const int nbox = g.n_int * g.n_int;
     const AxisGeom ag = axis_geom(g);
@@ -349,6 +358,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_attract(NodeLaunch a) {
 // written contiguously; caller-order outputs are scattered through perm.
 template <int K, bool EVAL>
 __global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a, int advance) {
+    pdl_wait();
+    pdl_trigger();
     DevState* st = a.st;
     const GridDesc g = st->grid;
     const AxisGeom ag = axis_geom(g);
@@ -437,6 +448,8 @@ __device__ __forceinline__ float kernel_of(float u, float gamma) {
 // go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic).
 template <int GI>
 __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advance) {
+    pdl_wait();
+    pdl_trigger();
     DevState* st = a.st;
     const long long t = st->iter;
     const int cur = (int)(t & 1);
@@ -492,6 +505,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
 // (row pointers, neighbour ids, neighbour positions) overlap.
 template <bool EVAL>
 __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int advance) {
+    pdl_wait();
+    pdl_trigger();
     DevState* st = a.st;
     const long long t = st->t_cur;
     const int cur = (int)(t & 1);
@@ -554,7 +569,7 @@ static inline int blocks_for(long long work, int threads) {
 }
 
 cudaError_t launch_order_reset(const NodeLaunch& a, int slot, cudaStream_t s) {
-    if (a.n == 0 || !a.rank) return cudaSuccess;
+    if (a.n == 0 || !a.vperm[slot]) return cudaSuccess;
     k_order_reset<<<blocks_for(a.n, kNodeThreads), kNodeThreads, 0, s>>>(a, slot);
     return cudaGetLastError();
 }
@@ -568,29 +583,27 @@ cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s) {
 }
 
 cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s) {
-    k_grid<<<1, 32, 0, s>>>(a, advance);
-    return cudaGetLastError();
+    return launch_pdl(k_grid, 1, 32, 0, s, a, advance);
 }
 
 cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
     if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
     const int nb = blocks_for(a.n, kNodeThreads);
-    k_bin<<<nb, kNodeThreads, 0, s>>>(a);
-    k_scan_lookback<<<scan_blocks, kScanThreads, 0, s>>>(a, scan_blocks, a.scan_status);
-    k_scatter<<<nb, kNodeThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(k_bin, nb, kNodeThreads, 0, s, a);
+    if (e == cudaSuccess) e = launch_pdl(k_scan_lookback, scan_blocks, kScanThreads, 0, s, a, scan_blocks, a.scan_status);
+    if (e == cudaSuccess) e = launch_pdl(k_scatter, nb, kNodeThreads, 0, s, a);
+    return e;
 }
 
 cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s) {
     const int bb = blocks_for(a.nbox_max, kNodeThreads);
     switch (a.k) {
-        case 1: k_spread<1><<<bb, kNodeThreads, 0, s>>>(a); break;
-        case 2: k_spread<2><<<bb, kNodeThreads, 0, s>>>(a); break;
-        case 3: k_spread<3><<<bb, kNodeThreads, 0, s>>>(a); break;
+        case 1: return launch_pdl(k_spread<1>, bb, kNodeThreads, 0, s, a);
+        case 2: return launch_pdl(k_spread<2>, bb, kNodeThreads, 0, s, a);
+        case 3: return launch_pdl(k_spread<3>, bb, kNodeThreads, 0, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s) {
@@ -602,30 +615,26 @@ cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s) {
 cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
     const int nb = blocks_for(a.n, 2 * kNodeThreads);
     switch (a.k) {
-        case 1: eval ? k_gather_update<1, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<1, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
-        case 2: eval ? k_gather_update<2, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<2, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
-        case 3: eval ? k_gather_update<3, true><<<nb, kNodeThreads, 0, s>>>(a, advance) : k_gather_update<3, false><<<nb, kNodeThreads, 0, s>>>(a, advance); break;
+        case 1: return launch_pdl(eval ? k_gather_update<1, true> : k_gather_update<1, false>, nb, kNodeThreads, 0, s, a, advance);
+        case 2: return launch_pdl(eval ? k_gather_update<2, true> : k_gather_update<2, false>, nb, kNodeThreads, 0, s, a, advance);
+        case 3: return launch_pdl(eval ? k_gather_update<3, true> : k_gather_update<3, false>, nb, kNodeThreads, 0, s, a, advance);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s) {
     dim3 grid(blocks_for(a.n, kNodeThreads), a.nchunks);
     switch (a.gamma_int) {
-        case 2: k_exact<2><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
-        case 4: k_exact<4><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
-        case 8: k_exact<8><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
-        default: k_exact<0><<<grid, kNodeThreads, 0, s>>>(a, advance); break;
+        case 2: return launch_pdl(k_exact<2>, grid, kNodeThreads, 0, s, a, advance);
+        case 4: return launch_pdl(k_exact<4>, grid, kNodeThreads, 0, s, a, advance);
+        case 8: return launch_pdl(k_exact<8>, grid, kNodeThreads, 0, s, a, advance);
+        default: return launch_pdl(k_exact<0>, grid, kNodeThreads, 0, s, a, advance);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_edge_update(const NodeLaunch& a, int advance, int eval, cudaStream_t s) {
     const int nb = blocks_for(a.n, 2 * kNodeThreads);
-    if (eval) k_edge_update<true><<<nb, kNodeThreads, 0, s>>>(a, advance);
-    else k_edge_update<false><<<nb, kNodeThreads, 0, s>>>(a, advance);
-    return cudaGetLastError();
+    return launch_pdl(eval ? k_edge_update<true> : k_edge_update<false>, nb, kNodeThreads, 0, s, a, advance);
 }
 
 }  // namespace tfdp

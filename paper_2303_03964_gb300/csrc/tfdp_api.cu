@@ -103,7 +103,6 @@ struct tfdp_graph {
     int2* keyslot = nullptr;
     int* vperm[2] = {nullptr, nullptr};
     float2* vxy[2] = {nullptr, nullptr};
-    int* rank = nullptr;
     bool last_was_eval = false;  // which visit-order buffer holds the latest sort
     float* gin = nullptr;
     float2* T1 = nullptr;
@@ -157,7 +156,6 @@ struct tfdp_graph {
         a.vperm[1] = vperm[1];
         a.vxy[0] = vxy[0];
         a.vxy[1] = vxy[1];
-        a.rank = (params.rep_mode == TFDP_REP_FFT) ? rank : nullptr;
         a.gin = gin;
         a.Gs = Gs;
         a.gout = gout;
@@ -263,7 +261,6 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     size_t o_vp1 = A.take(sizeof(int) * n);
     size_t o_vx0 = A.take(sizeof(float2) * n);
     size_t o_vx1 = A.take(sizeof(float2) * n);
-    size_t o_rank = A.take(sizeof(int) * n);
     size_t o_gin = A.take(sizeof(float) * 3 * (size_t)Gs * Gs);
     size_t o_T1 = A.take(sizeof(float2) * 3 * NH * ystride);
     size_t o_T2 = A.take(sizeof(float2) * 3 * NH * ystride);
@@ -287,7 +284,6 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->vperm[1] = (int*)(b + o_vp1);
     g->vxy[0] = (float2*)(b + o_vx0);
     g->vxy[1] = (float2*)(b + o_vx1);
-    g->rank = (int*)(b + o_rank);
     g->gin = (float*)(b + o_gin);
     g->T1 = (float2*)(b + o_T1);
     g->T2 = (float2*)(b + o_T2);
@@ -866,7 +862,7 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
         if (!fft_geometry(p, &P, &logP, &G_max, &nbox_max)) return TFDP_ERR_PARAM_RANGE;
         const size_t Gs = align_up((size_t)G_max, 4), ys = align_up((size_t)G_max, 32), NH = (size_t)P / 2 + 1;
         b += sizeof(int) * (align_up((size_t)nbox_max, 8192) + nbox_max + 1) + 8 * 1024;
-        b += nn * (sizeof(int2) + 2 * sizeof(int) + 2 * sizeof(float2) + sizeof(int));
+        b += nn * (sizeof(int2) + 2 * sizeof(int) + 2 * sizeof(float2));
         b += sizeof(float) * 3 * Gs * Gs + 2 * sizeof(float2) * 3 * NH * ys + sizeof(float4) * Gs * Gs;
         b += sizeof(float2) * 3 * NH * P + 3 * sizeof(float) * NH * P + sizeof(float2) * P + 32 * 256;
     }
