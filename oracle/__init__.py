@@ -34,10 +34,10 @@ def _lib():
         sigs = {
             "or_num_threads": ([], _i32),
             "or_tforce": ([_d, _d], _d),
-            "or_rep_exact": ([_i64, _p, _d, _i64, _i64, _p], None),
-            "or_rep_exact_rows": ([_i64, _p, _d, _i64, _p, _p], None),
-            "or_att": ([_i64, _i64, _p, _p, _d, _d, _p], None),
-            "or_energy": ([_i64, _p, _i64, _p, _d, _d, _d], _d),
+            "or_rep_exact": ([_i64, _p, _p, _d, _i64, _i64, _p], None),
+            "or_rep_exact_rows": ([_i64, _p, _p, _d, _i64, _p, _p], None),
+            "or_att": ([_i64, _i64, _p, _p, _p, _d, _d, _p], None),
+            "or_energy": ([_i64, _p, _i64, _p, _p, _p, _d, _d, _d], _d),
             "or_grid_policy": ([_i64, _p, _i32, _i32, _i32, _i32, _p], None),
             "or_box_f32": ([ctypes.c_float, ctypes.c_float, ctypes.c_float, _i32], _i32),
             "or_lagrange": ([_i32, _d, _p], None),
@@ -45,12 +45,12 @@ def _lib():
             "or_fft2": ([_i64, _p, _p, _i32], None),
             "or_conv_grid_fft": ([_i64, _i64, _d, _d, _i32, _p, _p], _i32),
             "or_conv_grid_direct": ([_i64, _d, _d, _i32, _p, _p], None),
-            "or_rep_fft": ([_i64, _p, _p, _d, _i32, _d, _d, _i32, _i64, _p], _i32),
+            "or_rep_fft": ([_i64, _p, _p, _p, _d, _i32, _d, _d, _i32, _i64, _p], _i32),
             "or_step_size": ([_i64, _i64, _d, _d], _d),
             "or_k_of_iter": ([_i32, _i64, _i64], _i32),
             "or_update": ([_i64, _p, _p, _d], None),
-            "or_iterate": ([_i64, _i64, _p, _p, _d, _d, _d, _i32, _i32, _i32, _i32, _i32, _i64,
-                            _d, _d, _i64, _i64, _i64], _i32),
+            "or_iterate": ([_i64, _i64, _p, _p, _p, _p, _d, _d, _d, _i32, _i32, _i32, _i32, _i32,
+                            _i64, _d, _d, _i64, _i64, _i64], _i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(lib, name)
@@ -80,34 +80,53 @@ def tforce(d: float, phi: float) -> float:
     return float(_lib().or_tforce(float(d), float(phi)))
 
 
-def rep_exact(xy, gamma: float, rows=None):
-    """Exact repulsion of Eq. (repfK), FP64. ``rows`` selects target rows (all by default)."""
+def _weights(w, n):
+    """Per-node local-refinement weights as a contiguous FP64 array (None: all 1)."""
+    if w is None:
+        return None
+    w = np.ascontiguousarray(np.asarray(w, dtype=np.float64).reshape(-1))
+    if w.shape[0] != n:
+        raise ValueError("one weight per node")
+    return w
+
+
+def _wptr(w):
+    return _ptr(w) if w is not None else None
+
+
+def rep_exact(xy, gamma: float, rows=None, w=None):
+    """Exact repulsion of Eq. (repfK), FP64. ``rows`` selects target rows (all by default);
+    ``w`` are per-node repulsion weights r_i (pair force scaled by r_i r_j)."""
     xy = _f64(xy).reshape(-1, 2)
     n = xy.shape[0]
+    w = _weights(w, n)
     if rows is None:
         out = np.zeros((n, 2))
-        _lib().or_rep_exact(n, _ptr(xy), gamma, 0, n, _ptr(out))
+        _lib().or_rep_exact(n, _ptr(xy), _wptr(w), gamma, 0, n, _ptr(out))
         return out
     rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
     out = np.zeros((rows.shape[0], 2))
-    _lib().or_rep_exact_rows(n, _ptr(xy), gamma, rows.shape[0], _ptr(rows), _ptr(out))
+    _lib().or_rep_exact_rows(n, _ptr(xy), _wptr(w), gamma, rows.shape[0], _ptr(rows), _ptr(out))
     return out
 
 
-def attraction(edges, xy, alpha: float, beta: float):
-    """alpha-weighted attraction of Eq. (newforce) over undirected ``edges`` (m x 2)."""
+def attraction(edges, xy, alpha: float, beta: float, w=None):
+    """alpha-weighted attraction of Eq. (newforce) over undirected ``edges`` (m x 2);
+    ``w`` are per-node attraction weights a_i (edge force scaled by a_i a_j)."""
     xy = _f64(xy).reshape(-1, 2)
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    w = _weights(w, xy.shape[0])
     out = np.zeros_like(xy)
-    _lib().or_att(xy.shape[0], e.shape[0], _ptr(e), _ptr(xy), alpha, beta, _ptr(out))
+    _lib().or_att(xy.shape[0], e.shape[0], _ptr(e), _ptr(xy), _wptr(w), alpha, beta, _ptr(out))
     return out
 
 
-def energy(xy, edges, alpha: float, beta: float, gamma: float) -> float:
+def energy(xy, edges, alpha: float, beta: float, gamma: float, wr=None, wa=None) -> float:
     xy = _f64(xy).reshape(-1, 2)
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
-    return float(_lib().or_energy(xy.shape[0], _ptr(xy), e.shape[0], _ptr(e), alpha, beta,
-                                  gamma))
+    wr, wa = _weights(wr, xy.shape[0]), _weights(wa, xy.shape[0])
+    return float(_lib().or_energy(xy.shape[0], _ptr(xy), e.shape[0], _ptr(e), _wptr(wr), _wptr(wa),
+                                  alpha, beta, gamma))
 
 
 def grid_policy(xy_f32, k: int, n_int_min: int = 50, grid_max: int = 1 << 30,
@@ -165,7 +184,7 @@ def conv_grid(channels, spacing: float, gamma: float, P=None, direct: bool = Fal
 
 
 def rep_fft(xy, gamma: float, k: int, grid=None, P=None, xy_f32=None, n_int_min: int = 50,
-            grid_max: int = 1 << 30, policy: int = GRID_SNAP_H):
+            grid_max: int = 1 << 30, policy: int = GRID_SNAP_H, w=None):
     """ibFFT repulsion of Sec. 3.4 (paper's three-sum form), FP64.
 
     ``grid`` is a dict (lo, h, n_int); when omitted it comes from ``grid_policy`` on the
@@ -183,8 +202,9 @@ def rep_fft(xy, gamma: float, k: int, grid=None, P=None, xy_f32=None, n_int_min:
         P = 1
         while P < 2 * G - 1:
             P *= 2
+    w = _weights(w, xy.shape[0])
     out = np.zeros_like(xy)
-    rc = _lib().or_rep_fft(xy.shape[0], _ptr(xy), _ptr(xyf), gamma, k, float(grid["lo"]),
+    rc = _lib().or_rep_fft(xy.shape[0], _ptr(xy), _ptr(xyf), _wptr(w), gamma, k, float(grid["lo"]),
                            float(grid["h"]), n_int, int(P), _ptr(out))
     if rc != 0:
         raise RuntimeError("or_rep_fft failed: %d" % rc)
@@ -210,14 +230,16 @@ def update(xy, D, s: float):
 
 def iterate(xy, edges, iters: int, alpha=0.1, beta=8.0, gamma=2.0, mode="exact", k=3,
             n_int_min=50, grid_max=1 << 30, policy=GRID_SNAP_H, P=0, s0=1.0, smin=0.01,
-            T=300, t0=0):
+            T=300, t0=0, wrep=None, watt=None):
     """Run ``iters`` synchronous t-FDP iterations from iteration index ``t0``; k = 0 takes
-    k per iteration from the dynamic strategy (``k_of_iter``)."""
+    k per iteration from the dynamic strategy (``k_of_iter``); ``wrep`` / ``watt`` are the
+    per-node local-refinement weights (None: all 1)."""
     xy = _f64(xy).reshape(-1, 2).copy()
     e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    wr, wa = _weights(wrep, xy.shape[0]), _weights(watt, xy.shape[0])
     m = {"exact": 0, "fft": 1}[mode]
-    rc = _lib().or_iterate(xy.shape[0], e.shape[0], _ptr(e), _ptr(xy), alpha, beta, gamma, m, k,
-                           n_int_min, grid_max, policy, P, s0, smin, T, t0, iters)
+    rc = _lib().or_iterate(xy.shape[0], e.shape[0], _ptr(e), _ptr(xy), _wptr(wr), _wptr(wa), alpha,
+                           beta, gamma, m, k, n_int_min, grid_max, policy, P, s0, smin, T, t0, iters)
     if rc != 0:
         raise RuntimeError("or_iterate failed: %d" % rc)
     return xy

@@ -21,6 +21,13 @@
  *                         (boundaries floor(0.9 T), floor(0.95 T): a reading)
  *   position update       Sec. 3.1 (move along the resultant force until convergence);
  *                         the step schedule is a reading, the paper gives none.
+ *   local refinement      Sec. 5 "Local Refinement" (fisheye views): stronger attraction
+ *                         between focal nodes and their neighbours, stronger repulsion
+ *                         elsewhere. The paper gives no formula; the reading is per-node
+ *                         weights r_i (repulsion) and a_i (attraction) with the pair
+ *                         repulsion scaled by r_i r_j and the edge attraction by a_i a_j,
+ *                         which keeps D = -grad E for the weighted energy below. Every
+ *                         weight argument may be NULL (all weights 1: the plain method).
  *
  * Sign convention (reading of Sec. 3.3/3.4): the functions return the displacement
  * direction of each node. Repulsion pushes node i away from j,
@@ -30,6 +37,9 @@
  * Their sum D(i) = frep(i) + fatt(i) is minus the gradient of
  *     E = sum_{i<j} (1+d^2)^(1-gamma) / (2(gamma-1))
  *       + alpha * sum_{edges} [ d^2/2 + (beta/2) ln(1+d^2) ].
+ * With local-refinement weights: frep(i) = r_i sum_j r_j K_ij (x_i - x_j),
+ * fatt(i) = alpha sum_{j <-> i} a_i a_j (...)(x_j - x_i), and each term of E carries the
+ * same product of weights.
  *
  * Floating point decides one integer here: the box that holds a node. Both this
  * oracle and the GPU library take that decision in IEEE FP32 with the same
@@ -64,13 +74,16 @@ int or_num_threads(void) {
 /* K(d^2) = (1 + d^2)^(-gamma), the kernel of Eq. (repfK). */
 static double or_kernel(double d2, double gamma) { return pow(1.0 + d2, -gamma); }
 
+/* Local-refinement weight of node i (1 without weights). */
+static double or_w(const double* w, int64_t i) { return w ? w[i] : 1.0; }
+
 /* f(d) = d / (1 + d^2)^phi, Eq. (forcefunction). Exposed for the pins. */
 double or_tforce(double d, double phi) { return d / pow(1.0 + d * d, phi); }
 
 /* ------------------------------------------------------------------------- */
 /* Exact repulsion, Eq. (repfK): rows [i0, i1) of the n x n sum (all sources). */
 /* ------------------------------------------------------------------------- */
-void or_rep_exact(int64_t n, const double* xy, double gamma, int64_t i0, int64_t i1,
+void or_rep_exact(int64_t n, const double* xy, const double* wr, double gamma, int64_t i0, int64_t i1,
                   double* frep /* 2*(i1-i0) */) {
     int64_t i;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -80,17 +93,17 @@ void or_rep_exact(int64_t n, const double* xy, double gamma, int64_t i0, int64_t
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double dx = xi - xy[2 * j], dy = yi - xy[2 * j + 1];
-            double K = or_kernel(dx * dx + dy * dy, gamma);
+            double K = or_w(wr, j) * or_kernel(dx * dx + dy * dy, gamma);
             fx += K * dx;
             fy += K * dy;
         }
-        frep[2 * (i - i0)] = fx;
-        frep[2 * (i - i0) + 1] = fy;
+        frep[2 * (i - i0)] = or_w(wr, i) * fx;
+        frep[2 * (i - i0) + 1] = or_w(wr, i) * fy;
     }
 }
 
 /* Same sum for an explicit list of target rows (row-sampled check at large n). */
-void or_rep_exact_rows(int64_t n, const double* xy, double gamma, int64_t nrows,
+void or_rep_exact_rows(int64_t n, const double* xy, const double* wr, double gamma, int64_t nrows,
                        const int64_t* rows, double* frep /* 2*nrows */) {
     int64_t r;
 #pragma omp parallel for schedule(dynamic, 4)
@@ -101,12 +114,12 @@ void or_rep_exact_rows(int64_t n, const double* xy, double gamma, int64_t nrows,
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double dx = xi - xy[2 * j], dy = yi - xy[2 * j + 1];
-            double K = or_kernel(dx * dx + dy * dy, gamma);
+            double K = or_w(wr, j) * or_kernel(dx * dx + dy * dy, gamma);
             fx += K * dx;
             fy += K * dy;
         }
-        frep[2 * r] = fx;
-        frep[2 * r + 1] = fy;
+        frep[2 * r] = or_w(wr, i) * fx;
+        frep[2 * r + 1] = or_w(wr, i) * fy;
     }
 }
 
@@ -114,13 +127,13 @@ void or_rep_exact_rows(int64_t n, const double* xy, double gamma, int64_t nrows,
 /* Attraction, Eq. (newforce) times alpha (resultant force, Sec. 3.3).        */
 /* edges: m undirected pairs (e[2q], e[2q+1]); each adds to both endpoints.   */
 /* ------------------------------------------------------------------------- */
-void or_att(int64_t n, int64_t m, const int32_t* edges, const double* xy, double alpha,
-            double beta, double* fatt /* 2n */) {
+void or_att(int64_t n, int64_t m, const int32_t* edges, const double* xy, const double* wa,
+            double alpha, double beta, double* fatt /* 2n */) {
     memset(fatt, 0, sizeof(double) * 2 * (size_t)n);
     for (int64_t q = 0; q < m; ++q) {
         int64_t i = edges[2 * q], j = edges[2 * q + 1];
         double dx = xy[2 * j] - xy[2 * i], dy = xy[2 * j + 1] - xy[2 * i + 1];
-        double c = alpha * (1.0 + beta / (1.0 + dx * dx + dy * dy));
+        double c = alpha * or_w(wa, i) * or_w(wa, j) * (1.0 + beta / (1.0 + dx * dx + dy * dy));
         fatt[2 * i] += c * dx;
         fatt[2 * i + 1] += c * dy;
         fatt[2 * j] -= c * dx;
@@ -129,15 +142,15 @@ void or_att(int64_t n, int64_t m, const int32_t* edges, const double* xy, double
 }
 
 /* Energy whose negative gradient is frep + fatt (reading of the sign, Sec. 3.3). */
-double or_energy(int64_t n, const double* xy, int64_t m, const int32_t* edges, double alpha,
-                 double beta, double gamma) {
+double or_energy(int64_t n, const double* xy, int64_t m, const int32_t* edges, const double* wr,
+                 const double* wa, double alpha, double beta, double gamma) {
     double rep = 0.0;
     int64_t i;
 #pragma omp parallel for reduction(+ : rep) schedule(dynamic, 16)
     for (i = 0; i < n; ++i) {
         for (int64_t j = i + 1; j < n; ++j) {
             double dx = xy[2 * i] - xy[2 * j], dy = xy[2 * i + 1] - xy[2 * j + 1];
-            rep += pow(1.0 + dx * dx + dy * dy, 1.0 - gamma) / (2.0 * (gamma - 1.0));
+            rep += or_w(wr, i) * or_w(wr, j) * pow(1.0 + dx * dx + dy * dy, 1.0 - gamma) / (2.0 * (gamma - 1.0));
         }
     }
     double att = 0.0;
@@ -145,7 +158,7 @@ double or_energy(int64_t n, const double* xy, int64_t m, const int32_t* edges, d
         int64_t a = edges[2 * q], b = edges[2 * q + 1];
         double dx = xy[2 * a] - xy[2 * b], dy = xy[2 * a + 1] - xy[2 * b + 1];
         double d2 = dx * dx + dy * dy;
-        att += 0.5 * d2 + 0.5 * beta * log1p(d2);
+        att += or_w(wa, a) * or_w(wa, b) * (0.5 * d2 + 0.5 * beta * log1p(d2));
     }
     return rep + alpha * att;
 }
@@ -360,8 +373,8 @@ void or_conv_grid_direct(int64_t G, double s, double gamma, int nch, const doubl
 /*  k interior equispaced nodes per box, spacing h/k across box borders).     */
 /*  xyf: FP32 positions used for the box decision only.                       */
 /* ------------------------------------------------------------------------- */
-int or_rep_fft(int64_t n, const double* xy, const float* xyf, double gamma, int k, double lo,
-               double h, int n_int, int64_t P, double* frep /* 2n */) {
+int or_rep_fft(int64_t n, const double* xy, const float* xyf, const double* wr, double gamma, int k,
+               double lo, double h, int n_int, int64_t P, double* frep /* 2n */) {
     int64_t G = (int64_t)n_int * k;
     size_t GG = (size_t)G * (size_t)G;
     double* ch = (double*)calloc(3 * GG, sizeof(double));   /* C_1, C_x, C_y */
@@ -383,7 +396,7 @@ int or_rep_fft(int64_t n, const double* xy, const float* xyf, double gamma, int 
         for (int ly = 0; ly < k; ++ly)
             for (int lx = 0; lx < k; ++lx) {
                 int64_t qy = (int64_t)box[2 * i + 1] * k + ly, qx = (int64_t)box[2 * i] * k + lx;
-                double w = wx[lx] * wy[ly];
+                double w = or_w(wr, i) * wx[lx] * wy[ly];  /* charge r_i per node */
                 size_t q = (size_t)qy * G + qx;
                 ch[q] += w;
                 ch[GG + q] += w * xy[2 * i];
@@ -409,8 +422,8 @@ int or_rep_fft(int64_t n, const double* xy, const float* xyf, double gamma, int 
                 px += w * psi[GG + q];
                 py += w * psi[2 * GG + q];
             }
-        frep[2 * i] = xy[2 * i] * p1 - px;
-        frep[2 * i + 1] = xy[2 * i + 1] * p1 - py;
+        frep[2 * i] = or_w(wr, i) * (xy[2 * i] * p1 - px);
+        frep[2 * i + 1] = or_w(wr, i) * (xy[2 * i + 1] * p1 - py);
     }
     free(ch); free(psi); free(box); free(wts);
     return 0;
@@ -460,9 +473,10 @@ int or_k_of_iter(int k, int64_t t, int64_t T) {
     return 3;
 }
 
-int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, double alpha, double beta,
-               double gamma, int mode, int k, int n_int_min, int grid_max, int policy, int64_t P,
-               double s0, double smin, int64_t T, int64_t t0, int64_t iters) {
+int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, const double* wr,
+               const double* wa, double alpha, double beta, double gamma, int mode, int k,
+               int n_int_min, int grid_max, int policy, int64_t P, double s0, double smin, int64_t T,
+               int64_t t0, int64_t iters) {
     double* frep = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
     double* fatt = (double*)malloc(sizeof(double) * 2 * (size_t)(n > 0 ? n : 1));
     float* xyf = (float*)malloc(sizeof(float) * 2 * (size_t)(n > 0 ? n : 1));
@@ -470,7 +484,7 @@ int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, double al
     int rc = 0;
     for (int64_t t = t0; t < t0 + iters && rc == 0; ++t) {
         if (mode == 0) {
-            or_rep_exact(n, xy, gamma, 0, n, frep);
+            or_rep_exact(n, xy, wr, gamma, 0, n, frep);
         } else {
             for (int64_t i = 0; i < 2 * n; ++i) xyf[i] = (float)xy[i];
             const int kt = or_k_of_iter(k, t, T);
@@ -478,9 +492,9 @@ int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, double al
             or_grid_policy(n, xyf, kt, n_int_min, grid_max, policy, g);
             int n_int = (int)g[2];
             int64_t PP = P > 0 ? P : or_nextpow2(2 * (int64_t)n_int * kt - 1);
-            rc = or_rep_fft(n, xy, xyf, gamma, kt, g[0], g[1], n_int, PP, frep);
+            rc = or_rep_fft(n, xy, xyf, wr, gamma, kt, g[0], g[1], n_int, PP, frep);
         }
-        or_att(n, m, edges, xy, alpha, beta, fatt);
+        or_att(n, m, edges, xy, wa, alpha, beta, fatt);
         for (int64_t i = 0; i < 2 * n; ++i) frep[i] += fatt[i];
         or_update(n, xy, frep, or_step_size(t, T, s0, smin));
     }

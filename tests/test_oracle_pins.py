@@ -374,3 +374,82 @@ def test_dynamic_k_iteration_is_the_fixed_k_segments():
     assert np.array_equal(dyn, x)
     # and differs from a fixed-k run, so the switch is not a no-op
     assert not np.array_equal(dyn, oracle.iterate(xy, e, 20, k=3, **kw))
+
+
+# ------------------------------------------------------------------ local refinement
+# Sec. 5 "Local Refinement" gives no formula; the reading is per-node weights with the
+# pair repulsion scaled by r_i r_j and the edge attraction by a_i a_j.
+
+def _weights(n, seed):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.5, 3.0, n), rng.uniform(0.5, 3.0, n)
+
+
+def test_unit_weights_are_the_plain_method():
+    e, xy = _random_graph(40, 90, 31)
+    one = np.ones(40)
+    assert np.array_equal(oracle.rep_exact(xy, 2.0, w=one), oracle.rep_exact(xy, 2.0))
+    assert np.array_equal(oracle.attraction(e, xy, 0.1, 8.0, w=one), oracle.attraction(e, xy, 0.1, 8.0))
+    assert np.array_equal(oracle.rep_fft(xy, 2.0, 3, w=one, n_int_min=4), oracle.rep_fft(xy, 2.0, 3, n_int_min=4))
+
+
+def test_weighted_forces_are_minus_grad_of_weighted_energy():
+    e, xy = _random_graph(12, 25, 32)
+    wr, wa = _weights(12, 33)
+    D = oracle.rep_exact(xy, 3.0, w=wr) + oracle.attraction(e, xy, 0.2, 5.0, w=wa)
+    g = np.zeros_like(xy)
+    eps = 1e-6
+    for i in range(12):
+        for c in range(2):
+            p, q = xy.copy(), xy.copy()
+            p[i, c] += eps
+            q[i, c] -= eps
+            g[i, c] = (oracle.energy(p, e, 0.2, 5.0, 3.0, wr=wr, wa=wa)
+                       - oracle.energy(q, e, 0.2, 5.0, 3.0, wr=wr, wa=wa)) / (2 * eps)
+    assert np.linalg.norm(D + g) <= 1e-7 * np.linalg.norm(D)
+
+
+def test_weighted_forces_are_antisymmetric():
+    e, xy = _random_graph(50, 120, 34)
+    wr, wa = _weights(50, 35)
+    fr = oracle.rep_exact(xy, 2.0, w=wr)
+    fa = oracle.attraction(e, xy, 0.1, 8.0, w=wa)
+    assert np.abs(fr.sum(0)).max() <= 1e-12 * np.abs(fr).sum()
+    assert np.abs(fa.sum(0)).max() <= 1e-12 * np.abs(fa).sum()
+
+
+@pytest.mark.parametrize("path", ["exact", "fft"])
+def test_repulsion_weight_two_is_a_duplicated_node(path):
+    """A source of weight 2 acts on every other node like two unit nodes at one point;
+    on itself, the force is twice the unit-weight force (both sides linear in r)."""
+    rng = np.random.default_rng(36)
+    n = 30
+    xy = rng.uniform(-6, 6, size=(n, 2))
+    w = np.ones(n)
+    w[0] = 2.0
+    dup = np.vstack([xy, xy[:1]])
+    if path == "exact":
+        fw = oracle.rep_exact(xy, 2.0, w=w)
+        fd = oracle.rep_exact(dup, 2.0)
+        f1 = oracle.rep_exact(xy, 2.0)
+    else:
+        kw = dict(k=3, n_int_min=5)
+        fw = oracle.rep_fft(xy, 2.0, w=w, **kw)
+        fd = oracle.rep_fft(dup, 2.0, **kw)
+        f1 = oracle.rep_fft(xy, 2.0, **kw)
+    assert np.allclose(fw[1:], fd[1:n], rtol=0, atol=1e-12 * np.abs(fd).max())
+    # node 0 with r_0 = 2: 2 x (sum over unit sources) -- its duplicate adds no force
+    assert np.allclose(fw[0], 2.0 * f1[0], rtol=1e-12, atol=1e-14)
+
+
+def test_weighted_two_node_equilibrium():
+    """Two connected nodes balance where r1 r2 (1+d^2)^-gamma = alpha a1 a2 (1 + beta/(1+d^2)),
+    i.e. the unweighted equilibrium with alpha' = alpha a1 a2 / (r1 r2)."""
+    wr, wa = np.array([1.5, 2.0]), np.array([0.8, 1.25])
+    alpha = 0.1 * wa.prod() / wr.prod()
+    d_star = _equilibrium_distance(alpha, 8.0, 2.0)
+    xy = np.array([[0.0, 0.0], [2.0, 0.5]])
+    e = np.array([[0, 1]], np.int32)
+    x = oracle.iterate(xy, e, 3000, alpha=0.1, beta=8.0, gamma=2.0, mode="exact", T=3000,
+                       s0=0.05, smin=1e-4, wrep=wr, watt=wa)
+    assert abs(np.linalg.norm(x[0] - x[1]) - d_star) < 1e-6
