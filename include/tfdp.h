@@ -208,6 +208,23 @@ tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable);
  * TFDP_ERR_INVALID_ARG if timing is off. */
 tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages);
 
+/* Local refinement (Sec. 5 "Local Refinement", fisheye views): per-node weights. The
+ * repulsion between nodes i and j is scaled by w_rep[i] * w_rep[j] and the attraction
+ * along edge (i, j) by w_att[i] * w_att[j]. The paper describes the effect (stronger
+ * attraction between focal nodes and their neighbours, stronger repulsion elsewhere),
+ * not a formula; the products are a reading that keeps the forces the negative gradient
+ * of one energy. Both paths (exact and ibFFT) apply them; the ibFFT spreads r_j as the
+ * charge of node j.
+ *   w_rep, w_att  n floats each in caller order, in host memory (on_device = 0) or device
+ *                 memory (on_device = 1), finite and in [0, TFDP_WEIGHT_MAX]; NULL resets
+ *                 that kind to 1 (the plain method). Copied; the caller keeps ownership.
+ * Takes effect from the next iteration or force evaluation (synchronises the stream and
+ * recaptures the iteration graphs). The library keeps up to 12 n bytes for the weights,
+ * which tfdp_graph_footprint does not count. TFDP_ERR_PARAM_RANGE if a weight is out of
+ * range (nothing changes). Batches and served jobs take no weights. */
+#define TFDP_WEIGHT_MAX 64.0f
+tfdp_status tfdp_set_node_weights(tfdp_graph* g, const float* w_rep, const float* w_att, int on_device);
+
 /* Wait for all work queued on the graph's stream. */
 tfdp_status tfdp_synchronize(tfdp_graph* g);
 

@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
                 // attraction of caller-order node gv (rowptr holds local offsets)
                 const float2 pi = a.xy[cur][gv];
                 a.fatt[gv] = attraction(v, pi, a.rowptr + G.rowptr_off, a.col + G.col_off, a.xy[cur],
-                                        (float)a.prm[g].alpha, (float)a.prm[g].beta);
+                                        (float)a.prm[g].alpha, (float)a.prm[g].beta, nullptr);
             }
         }
         grid.sync();
@@ -215,7 +215,8 @@ __global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
                 const int by = b / gd.n_int;
                 const int bx = b - by * gd.n_int;
                 const float2* sxy = a.vxy[(int)(st->t_cur & 1) ^ 1] + G.node_off;
-                spread_box<K>(sxy, max(G.off[b], 0), min(G.off[b + 1], G.n), bx, by, axis_geom(gd), G.gin, G.Gs);
+                spread_box<K>(sxy, nullptr, max(G.off[b], 0), min(G.off[b + 1], G.n), bx, by, axis_geom(gd), G.gin,
+                              G.Gs);
             }
         }
         grid.sync();
@@ -486,6 +487,7 @@ tfdp_status upload_batch_params(tfdp_batch* b) {
         d.log2P = b->logP;
         const double r = std::floor(p.gamma + 0.5);
         d.gamma_int = (p.gamma == r && r >= 2.0 && r <= 8.0) ? (int)r : 0;
+        d.spread_shift = 0;  // no local-refinement weights in a batch
         d.step_table = b->d_steps + (size_t)g * b->T_max;
         const int T = p.total_iters;
         for (int t = 0; t < T; ++t)

@@ -64,6 +64,7 @@ struct DevParams {
     int P;           // FFT size per axis
     int log2P;
     int gamma_int;   // gamma if it is a small integer (2..8), else 0
+    int spread_shift; // fixed-point scale of the spread sums is 2^(27 - spread_shift)
     const double* step_table;  // s_t for t = 0 .. total_iters - 1 (host-computed, FP64)
 };
 
@@ -80,6 +81,8 @@ struct GridDesc {
     int n_int;
     int G;
     int k;          // interpolation nodes per box and axis in this iteration
+    float q_scale;  // fixed-point scale of the spread sums (2^(27 - spread_shift))
+    float q_inv;    // 1 / q_scale
 };
 
 // k of iteration t of a T-iteration run (Sec. 3.4 "Choices of k"). k > 0 is fixed;
@@ -165,6 +168,8 @@ __device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevP
     g.n_int = n_int;
     g.G = n_int * k;
     g.k = k;
+    g.q_scale = ldexpf(1.0f, 27 - p.spread_shift);
+    g.q_inv = ldexpf(1.0f, p.spread_shift - 27);
     return g;
 }
 

@@ -44,6 +44,10 @@ struct NodeLaunch {
     float2* xy[2];         // ping-pong positions; iteration t reads xy[t & 1]
     const int* rowptr;     // n + 1
     const int* col;        // 2m
+    // local refinement (per-node weights, caller order); nullptr: every weight is 1
+    const float* wrep;     // n, repulsion weight r_i (pair force scaled by r_i r_j)
+    const float* watt;     // n, attraction weight a_i (edge force scaled by a_i a_j)
+    float* vwr;            // n, r_i in the cell-sorted order (written by the sort) or nullptr
     DevState* st;
     const DevParams* prm;
     // FFT path

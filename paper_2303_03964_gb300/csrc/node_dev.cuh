@@ -13,6 +13,7 @@ namespace tfdp {
 // ---------------------------------------------------------------- box geometry
 struct AxisGeom {
     float lo, h_hi, h_lo, hk;  // origin, box side as hi + lo FP32 pair, h / k
+    float q_scale, q_inv;      // fixed-point scale of the spread sums and its inverse
     int n_int;
 };
 
@@ -22,6 +23,8 @@ __device__ __forceinline__ AxisGeom axis_geom(const GridDesc& g) {
     a.h_hi = g.h_f;
     a.h_lo = g.h_lo_f;
     a.hk = g.hk_f;
+    a.q_scale = g.q_scale;
+    a.q_inv = g.q_inv;
     a.n_int = g.n_int;
     return a;
 }
@@ -61,9 +64,10 @@ __device__ __forceinline__ float rcp_fast(float x) {
     return r;
 }
 
+// With local-refinement weights wa (nullptr: all 1) the edge (i, j) is scaled by a_i a_j.
 __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
                                              const int* __restrict__ col, const float2* __restrict__ xy,
-                                             float alpha, float beta) {
+                                             float alpha, float beta, const float* __restrict__ wa) {
     float fx = 0.0f, fy = 0.0f;
     int e = rowptr[i];
     const int e1 = rowptr[i + 1];
@@ -75,22 +79,29 @@ __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restr
         for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
+        float wj[4] = {1.0f, 1.0f, 1.0f, 1.0f};
+        if (wa) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) wj[u] = __ldg(wa + j[u]);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float dx = q[u].x - p.x, dy = q[u].y - p.y;
-            const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            const float c = wj[u] * fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
             fx = fmaf(c, dx, fx);
             fy = fmaf(c, dy, fy);
         }
     }
     for (; e < e1; ++e) {
-        const float2 q = xy[__ldg(col + e)];
+        const int j = __ldg(col + e);
+        const float2 q = xy[j];
         const float dx = q.x - p.x, dy = q.y - p.y;
-        const float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+        const float c = (wa ? __ldg(wa + j) : 1.0f) * fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
         fx = fmaf(c, dx, fx);
         fy = fmaf(c, dy, fy);
     }
-    return make_float2(alpha * fx, alpha * fy);
+    const float s = wa ? alpha * __ldg(wa + i) : alpha;
+    return make_float2(s * fx, s * fy);
 }
 
 // x + D min(1, s / |D|)
@@ -133,19 +144,18 @@ __device__ __forceinline__ void grid_decide(DevState* st, const DevParams& prm, 
 }
 
 // ---------------------------------------------------------------- spread and gather
-// Fixed-point scale of the spread sums. Each term w (|w| <= 3.52 for k <= 3, since a
-// 1D Lagrange weight on [0, 1) is at most 1.875) and w d / h (|d| <= 1.5 h) is rounded
-// to an int32 multiple of 2^-27 and summed in int64: the sums are exact, so they do not
-// depend on the order of the nodes in a box (which the parallel sort leaves open) and
-// every iteration is bitwise reproducible. The quantum 2^-27 = 7.5e-9 is far below the
-// FP32 resolution of the results.
-constexpr float kSpreadScale = 134217728.0f;       // 2^27
-constexpr float kSpreadInvScale = 1.0f / 134217728.0f;
+// Fixed-point spread sums. Each term w (|w| <= 3.52 for k <= 3, since a 1D Lagrange
+// weight on [0, 1) is at most 1.875) and w d / h (|d| <= 1.5 h), times the node's
+// repulsion weight r <= 2^spread_shift, is rounded to an int32 multiple of
+// 2^-(27 - spread_shift) (the grid's q_inv) and summed in int64: the sums are exact, so
+// they do not depend on the order of the nodes in a box (which the parallel sort leaves
+// open) and every iteration is bitwise reproducible. Without weights the quantum is
+// 2^-27 = 7.5e-9, far below the FP32 resolution of the results.
 
 __device__ __forceinline__ long long spread_q(float v) {
     // round to nearest even; a float-to-integer conversion saturates to the int32 range
     // by itself (in-box terms stay below 2^30), so no clamp is needed to keep it defined
-    return (long long)__float2int_rn(v * kSpreadScale);
+    return (long long)__float2int_rn(v);
 }
 
 // int64 -> FP32 rounded to nearest even, equal to (float)v, in 32-bit integer and FP32
@@ -165,10 +175,12 @@ __device__ __forceinline__ float ll2f_rn(long long v) {
 
 // Lagrange projection (Sec. 3.4 step 1) of the nodes sxy[s0, s1) of box (bx, by) onto its
 // K x K grid nodes: rho = sum w, m^x = sum w (x - y^x), m^y = sum w (y - y^y), written to
-// the three planes of gin (row stride Gs, plane stride Gs^2).
+// the three planes of gin (row stride Gs, plane stride Gs^2). With local-refinement
+// weights vw (sorted order; nullptr: all 1) each node's charge is r w.
 template <int K>
-__device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s0, int s1, int bx, int by,
-                                           const AxisGeom& ag, float* __restrict__ gin, int Gs) {
+__device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, const float* __restrict__ vw, int s0,
+                                           int s1, int bx, int by, const AxisGeom& ag, float* __restrict__ gin,
+                                           int Gs) {
     const size_t plane = (size_t)Gs * Gs;
     long long rho[K][K], mx[K][K], my[K][K];  // fixed point; moments in units of h
 #pragma unroll
@@ -180,8 +192,13 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
     for (int s = s0; s < s1; s += 2) {
         const bool two = s + 1 < s1;
         float2 pp[2];
+        float rr[2] = {ag.q_scale, ag.q_scale};  // node weight times the fixed-point scale
         pp[0] = sxy[s];
         pp[1] = two ? sxy[s + 1] : pp[0];
+        if (vw) {
+            rr[0] *= vw[s];
+            rr[1] *= two ? vw[s + 1] : 1.0f;
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             if (u == 1 && !two) break;
@@ -196,6 +213,7 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
             for (int l = 0; l < K; ++l) {
                 dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
                 dy[l] = (oy - ((float)l + 0.5f) * ag.hk) * inv_h;
+                wy[l] *= rr[u];  // the scale is a power of two: exact without weights
             }
 #pragma unroll
             for (int ly = 0; ly < K; ++ly)
@@ -208,13 +226,13 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, int s
                 }
         }
     }
-    const float hs = ag.h_hi * kSpreadInvScale;
+    const float hs = ag.h_hi * ag.q_inv;
 #pragma unroll
     for (int ly = 0; ly < K; ++ly)
 #pragma unroll
         for (int lx = 0; lx < K; ++lx) {
             const size_t q = (size_t)(by * K + ly) * Gs + (bx * K + lx);
-            gin[q] = ll2f_rn(rho[ly][lx]) * kSpreadInvScale;
+            gin[q] = ll2f_rn(rho[ly][lx]) * ag.q_inv;
             gin[plane + q] = ll2f_rn(mx[ly][lx]) * hs;
             gin[2 * plane + q] = ll2f_rn(my[ly][lx]) * hs;
         }

@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
         }
         nxy[pos] = vxy[v];
         nperm[pos] = i;
+        if (a.vwr) a.vwr[pos] = a.wrep[i];
     }
 }
 
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(kNodeThreads, 3) k_spread(NodeLaunch a) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nbox; b += gridDim.x * blockDim.x) {
         const int by = b / g.n_int;
         const int bx = b - by * g.n_int;
-        spread_box<K>(sxy, max(a.off[b], 0), min(a.off[b + 1], a.n), bx, by, ag, a.gin, a.Gs);
+        spread_box<K>(sxy, a.vwr, max(a.off[b], 0), min(a.off[b + 1], a.n), bx, by, ag, a.gin, a.Gs);
     }
 }
 
@@ -344,7 +345,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_attract(NodeLaunch a) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) pp[u] = xin[ii[u] < a.n ? ii[u] : base];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) fa[u] = attraction(ii[u] < a.n ? ii[u] : base, pp[u], a.rowptr, a.col, xin, alpha, beta);
+        for (int u = 0; u < 2; ++u)
+            fa[u] = attraction(ii[u] < a.n ? ii[u] : base, pp[u], a.rowptr, a.col, xin, alpha, beta, a.watt);
 #pragma unroll
         for (int u = 0; u < 2; ++u)
             if (ii[u] < a.n) a.fatt_out[ii[u]] = fa[u];
@@ -390,6 +392,14 @@ __global__ void __launch_bounds__(kNodeThreads) k_gather_update(NodeLaunch a, in
         float2 fr[2];
 #pragma unroll
         for (int u = 0; u < 2; ++u) fr[u] = gather_frep<K>(p[u], ag, a.gout, a.Gs);
+        if (a.vwr) {  // local refinement: frep(i) = r_i sum_j r_j (...)
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const float r = a.vwr[ss[u] < a.n ? ss[u] : base];
+                fr[u].x *= r;
+                fr[u].y *= r;
+            }
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int s = ss[u], i = ii[u];
@@ -446,7 +456,7 @@ __device__ __forceinline__ float kernel_of(float u, float gamma) {
 // Tiled all-pairs repulsion: each CTA owns kNodeThreads targets and one chunk of the
 // sources (blockIdx.y), staging source tiles in shared memory. Partial sums per chunk
 // go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic).
-template <int GI>
+template <int GI, bool W>
 __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advance) {
     pdl_wait();
     pdl_trigger();
@@ -466,6 +476,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
     }
     const float gamma = (float)a.prm->gamma;
     __shared__ float2 tile[kNodeThreads];
+    __shared__ float tile_w[W ? kNodeThreads : 1];  // source weights r_j (local refinement)
     const int i = blockIdx.x * kNodeThreads + threadIdx.x;
     const float2 pi = (i < a.n) ? xy[i] : make_float2(0.f, 0.f);
     const int csize = (a.n + a.nchunks - 1) / a.nchunks;
@@ -475,6 +486,7 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
     for (int s0 = j0; s0 < j1; s0 += kNodeThreads) {
         const int j = s0 + threadIdx.x;
         tile[threadIdx.x] = (j < j1) ? xy[j] : pi;
+        if (W) tile_w[threadIdx.x] = (j < j1) ? a.wrep[j] : 0.0f;
         __syncthreads();
         const int cnt = min(kNodeThreads, j1 - s0);
         if (cnt == kNodeThreads) {
@@ -482,7 +494,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
             for (int jj = 0; jj < kNodeThreads; ++jj) {
                 const float2 q = tile[jj];
                 const float dx = pi.x - q.x, dy = pi.y - q.y;
-                const float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                if (W) K *= tile_w[jj];
                 fx = fmaf(K, dx, fx);
                 fy = fmaf(K, dy, fy);
             }
@@ -490,7 +503,8 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
             for (int jj = 0; jj < cnt; ++jj) {
                 const float2 q = tile[jj];
                 const float dx = pi.x - q.x, dy = pi.y - q.y;
-                const float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+                if (W) K *= tile_w[jj];
                 fx = fmaf(K, dx, fx);
                 fy = fmaf(K, dy, fy);
             }
@@ -529,12 +543,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
                 fr[u].x += v.x;
                 fr[u].y += v.y;
             }
+            if (a.wrep) {  // local refinement: frep(i) = r_i sum_j r_j (...)
+                fr[u].x *= a.wrep[i];
+                fr[u].y *= a.wrep[i];
+            }
             pp[u] = xin[i];
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
             const int i = ii[u] < a.n ? ii[u] : base;
-            fa[u] = attraction(i, pp[u], a.rowptr, a.col, xin, alpha, beta);
+            fa[u] = attraction(i, pp[u], a.rowptr, a.col, xin, alpha, beta, a.watt);
         }
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -549,7 +567,6 @@ __global__ void __launch_bounds__(kNodeThreads) k_edge_update(NodeLaunch a, int 
                 const float2 q = capped_step(pp[u], make_float2(fr[u].x + fa[u].x, fr[u].y + fa[u].y), step);
                 if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
                 xout[i] = q;
-
                 mn = fminf(mn, fminf(q.x, q.y));
                 mx = fmaxf(mx, fmaxf(q.x, q.y));
             }
@@ -625,10 +642,10 @@ cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStre
 cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s) {
     dim3 grid(blocks_for(a.n, kNodeThreads), a.nchunks);
     switch (a.gamma_int) {
-        case 2: return launch_pdl(k_exact<2>, grid, kNodeThreads, 0, s, a, advance);
-        case 4: return launch_pdl(k_exact<4>, grid, kNodeThreads, 0, s, a, advance);
-        case 8: return launch_pdl(k_exact<8>, grid, kNodeThreads, 0, s, a, advance);
-        default: return launch_pdl(k_exact<0>, grid, kNodeThreads, 0, s, a, advance);
+        case 2: return launch_pdl(a.wrep ? k_exact<2, true> : k_exact<2, false>, grid, kNodeThreads, 0, s, a, advance);
+        case 4: return launch_pdl(a.wrep ? k_exact<4, true> : k_exact<4, false>, grid, kNodeThreads, 0, s, a, advance);
+        case 8: return launch_pdl(a.wrep ? k_exact<8, true> : k_exact<8, false>, grid, kNodeThreads, 0, s, a, advance);
+        default: return launch_pdl(a.wrep ? k_exact<0, true> : k_exact<0, false>, grid, kNodeThreads, 0, s, a, advance);
     }
 }
 

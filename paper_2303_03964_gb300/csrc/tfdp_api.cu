@@ -104,6 +104,12 @@ struct tfdp_graph {
     int* vperm[2] = {nullptr, nullptr};
     float2* vxy[2] = {nullptr, nullptr};
     bool last_was_eval = false;  // which visit-order buffer holds the latest sort
+    // local refinement: per-node weights (caller order) and r_i in sorted order
+    float* wrep = nullptr;
+    float* watt = nullptr;
+    float* vwr = nullptr;
+    bool use_wrep = false, use_watt = false;
+    int spread_shift = 0;  // fixed-point scale of the spread: 2^(27 - spread_shift)
     float* gin = nullptr;
     float2* T1 = nullptr;
     float2* T2 = nullptr;
@@ -144,6 +150,9 @@ struct tfdp_graph {
         a.xy[1] = xy[1];
         a.rowptr = rowptr;
         a.col = col;
+        a.wrep = use_wrep ? wrep : nullptr;
+        a.watt = use_watt ? watt : nullptr;
+        a.vwr = (use_wrep && params.rep_mode == TFDP_REP_FFT) ? vwr : nullptr;
         a.st = dst;
         a.prm = dprm;
         a.nbox_max = nbox_max;
@@ -339,6 +348,7 @@ tfdp_status upload_params(tfdp_graph* g) {
                        g->stream));
     g->dp = make_dev_params(g->params, g->P ? g->P : 128, g->logP ? g->logP : 7);
     g->dp.step_table = g->step_table;
+    g->dp.spread_shift = g->spread_shift;
     CK(cudaMemcpyAsync(g->dprm, &g->dp, sizeof(DevParams), cudaMemcpyHostToDevice, g->stream));
     // dp lives in the graph object, which outlives the copy; the copy is ordered
     // before any later kernel on the stream.
@@ -790,6 +800,46 @@ tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
     return TFDP_OK;
 }
 
+tfdp_status tfdp_set_node_weights(tfdp_graph* g, const float* w_rep, const float* w_att, int on_device) {
+    if (!g) return TFDP_ERR_INVALID_ARG;
+    const size_t n = (size_t)g->n;
+    if (n == 0) return TFDP_OK;
+    // validate both arrays before anything changes
+    std::vector<float> h[2];
+    float wmax[2] = {0.0f, 0.0f};
+    const float* src[2] = {w_rep, w_att};
+    for (int q = 0; q < 2; ++q) {
+        if (!src[q]) continue;
+        h[q].resize(n);
+        if (on_device) CK(cudaMemcpy(h[q].data(), src[q], sizeof(float) * n, cudaMemcpyDeviceToHost));
+        else std::memcpy(h[q].data(), src[q], sizeof(float) * n);
+        for (size_t i = 0; i < n; ++i) {
+            const float v = h[q][i];
+            if (!(v >= 0.0f && v <= TFDP_WEIGHT_MAX)) return TFDP_ERR_PARAM_RANGE;  // also NaN
+            wmax[q] = std::max(wmax[q], v);
+        }
+    }
+    CK(cudaStreamSynchronize(g->stream));  // no queued iteration still reads the old weights
+    float** dst[2] = {&g->wrep, &g->watt};
+    for (int q = 0; q < 2; ++q) {
+        if (!src[q]) continue;
+        if (!*dst[q]) CK(cudaMalloc(dst[q], sizeof(float) * n));
+        CK(cudaMemcpy(*dst[q], h[q].data(), sizeof(float) * n, cudaMemcpyHostToDevice));
+    }
+    if (w_rep && !g->vwr) CK(cudaMalloc(&g->vwr, sizeof(float) * n));
+    g->use_wrep = w_rep != nullptr;
+    g->use_watt = w_att != nullptr;
+    // spread terms scale with r <= 2^spread_shift; the fixed-point scale shrinks to match
+    int shift = 0;
+    while (g->use_wrep && (float)(1 << shift) < wmax[0]) ++shift;
+    g->spread_shift = shift;
+    free_execs(g);  // the captured kernels carry the weight pointers
+    tfdp_status st = upload_params(g);
+    if (st != TFDP_OK) return st;
+    CK(cudaStreamSynchronize(g->stream));
+    return TFDP_OK;
+}
+
 tfdp_status tfdp_set_stage_timing_mask(tfdp_graph* g, uint32_t mask) {
     if (!g) return TFDP_ERR_INVALID_ARG;
     mask &= (1u << TFDP_NUM_STAGES) - 1u;
@@ -887,6 +937,9 @@ tfdp_status tfdp_destroy_graph(tfdp_graph* g) {
     }
     if (g->fft_mem) cudaFree(g->fft_mem);
     if (g->node_mem) cudaFree(g->node_mem);
+    if (g->wrep) cudaFree(g->wrep);
+    if (g->watt) cudaFree(g->watt);
+    if (g->vwr) cudaFree(g->vwr);
     if (g->step_table) cudaFree(g->step_table);
     if (g->side_stream) cudaStreamSynchronize(g->side_stream);
     if (g->fork_ev) cudaEventDestroy(g->fork_ev);

@@ -17,6 +17,7 @@ REP_EXACT, REP_FFT = 0, 1
 PREC_FP32, PREC_BF16X3 = 0, 1
 GRID_PAPER, GRID_SNAP_H = 0, 1
 K_DYNAMIC = 0  # k_interp: the dynamic k schedule (1, then 2, then 3)
+WEIGHT_MAX = 64.0  # largest local-refinement weight
 DEBUG_GRID_CHARGES, DEBUG_GRID_OUTPUT, DEBUG_SORT_PERM, DEBUG_CELL_START = 1, 2, 3, 4
 STAGES = ["sort", "spread", "spectrum", "rows_fwd", "cols", "rows_inv", "gather_update",
           "exact", "edge_update", "attract"]
@@ -70,6 +71,7 @@ _SIGS = {
     "tfdp_set_params": ([_p, ctypes.POINTER(Params)], ctypes.c_int),
     "tfdp_get_params": ([_p, ctypes.POINTER(Params)], ctypes.c_int),
     "tfdp_set_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_set_node_weights": ([_p, _p, _p, ctypes.c_int], ctypes.c_int),
     "tfdp_get_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
     "tfdp_iterate": ([_p, ctypes.c_int32], ctypes.c_int),
     "tfdp_set_iteration": ([_p, ctypes.c_int64], ctypes.c_int),
@@ -212,6 +214,26 @@ class Graph:
         else:
             a = _host_f32(xy, self.n)
             _check(lib.tfdp_set_positions(self._h, a.ctypes.data_as(_p), 0), "tfdp_set_positions")
+
+    def set_node_weights(self, w_rep=None, w_att=None):
+        """Local-refinement weights (n each; None: all 1): repulsion between i and j scaled by
+        w_rep[i] w_rep[j], attraction along edge (i, j) by w_att[i] w_att[j]. Both numpy
+        (host) or both CUDA tensors (device)."""
+        dev = _is_torch_cuda(w_rep) or _is_torch_cuda(w_att)
+        keep, ptrs = [], []
+        for w in (w_rep, w_att):
+            if w is None:
+                ptrs.append(None)
+            elif dev:
+                assert _is_torch_cuda(w) and w.is_contiguous() and w.numel() == self.n
+                ptrs.append(_p(w.data_ptr()))
+            else:
+                a = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
+                if a.shape[0] != self.n:
+                    raise ValueError("one weight per node")
+                keep.append(a)
+                ptrs.append(a.ctypes.data_as(_p))
+        _check(lib.tfdp_set_node_weights(self._h, ptrs[0], ptrs[1], 1 if dev else 0), "tfdp_set_node_weights")
 
     def get_positions(self, out=None):
         """Positions as an (n, 2) float32 numpy array, or into `out` (numpy or CUDA tensor)."""
