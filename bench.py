@@ -378,6 +378,32 @@ def dynamic_k_measurement(e, xy, spec, stream, sampler=None):
     return out
 
 
+def quality_measurement():
+    """Layout quality of the ibFFT path against the exact path (Sec. 4 metrics): three
+    synthetic graphs, 300-iteration layouts from the same start, host-side metrics."""
+    import numpy as np
+    from paper_2303_03964_gb300 import quality as q
+    from paper_2303_03964_gb300 import synth, tfdp
+    rng = synth.rng_for(6)
+    graphs = []
+    e, _ = synth.sbm(2000, 10, 8.0, 0.9, rng)
+    graphs.append(("sbm_2000", 2000, e))
+    graphs.append(("lattice_40x40", 1600, synth.lattice(40, 40)))
+    graphs.append(("ba_2000", 2000, synth.barabasi_albert(2000, 2, rng)))
+    out = {"workload": "SBM n=2000 (10 blocks, mean degree 8), 40x40 lattice, BA n=2000 (m0=2); "
+                       "300 iterations, k=3, grid <= 255; relative = (ibFFT - exact) / exact"}
+    for name, n, e in graphs:
+        xy0 = synth.uniform_positions(n, np.sqrt(n) / 2.0, rng)
+        m = {}
+        for label, rep in (("exact", tfdp.REP_EXACT), ("ibfft", tfdp.REP_FFT)):
+            with tfdp.Graph(n, e, xy0, tfdp.params_default(rep_mode=rep, total_iters=300, grid_max=255)) as g:
+                g.iterate(300)
+                m[label] = q.evaluate(g.get_positions(), e)
+        m["relative"] = {k: q.relative(m["ibfft"][k], m["exact"][k]) for k in m["exact"]}
+        out[name] = m
+    return out
+
+
 def cpu_baseline(e, xy, spec, budget_s=15.0):
     """The FP64 oracle as it stands, on the same workload, on this host's cores."""
     import numpy as np
@@ -607,6 +633,9 @@ def run_ours(args):
     serving = None
     if not args.no_serving and args.workload == "lattice_1m":
         serving = serving_measurement(sampler=sampler)
+    quality = None
+    if not args.no_quality and args.workload == "lattice_1m":
+        quality = quality_measurement()
     dynamic_k = None
     if not args.no_dynamic_k and spec["rep"] == "fft":
         dynamic_k = dynamic_k_measurement(e, xy, spec, stream, sampler=sampler)
@@ -627,6 +656,7 @@ def run_ours(args):
         "batched": batched,
         "serving": serving,
         "dynamic_k": dynamic_k,
+        "quality": quality,
         "stages_ms": mean_stage,
         "stages_note": "5 steps after the timed region with every stage bracketed by events "
                        "(the timed steps bracket only the roofline kernel)",
@@ -655,6 +685,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-quality", action="store_true",
+                    help="skip the exact-vs-ibFFT layout-quality comparison")
     ap.add_argument("--no-dynamic-k", action="store_true",
                     help="skip the whole-layout comparison of the dynamic k schedule with k = 3")
     args = ap.parse_args()

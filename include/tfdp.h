@@ -232,7 +232,9 @@ tfdp_status tfdp_synchronize(tfdp_graph* g);
 tfdp_status tfdp_graph_set_stream(tfdp_graph* g, void* stream);
 
 /* Device bytes tfdp_create_graph would allocate for n nodes, m edges and `params`
- * (NULL = defaults), within a few KB; used for admission by memory footprint. */
+ * (NULL = defaults): an upper bound, above the allocation by at most a few KB plus
+ * 4 bytes per node of degree <= 32 counted in the bound 2m/33 on the hubs (the degrees
+ * are not known here); used for admission by memory footprint. */
 tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params, size_t* bytes);
 
 /* Free the graph and its device memory (synchronises first). NULL is a no-op. */

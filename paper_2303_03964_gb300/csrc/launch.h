@@ -37,6 +37,11 @@ int fft_rows_per_cta(int logP);
 cudaError_t prepare_fft(int logP);
 
 // Buffers of the node stages (node_kernels.cu).
+// Degree above which the attraction of a node is summed by a warp instead of a thread
+// (scale-free graphs have hubs whose neighbour lists a single thread would walk for
+// milliseconds).
+constexpr int kHeavyDegree = 32;
+
 struct NodeLaunch {
     int n;
     int k;                 // interpolation nodes per box and axis
@@ -48,6 +53,9 @@ struct NodeLaunch {
     const float* wrep;     // n, repulsion weight r_i (pair force scaled by r_i r_j)
     const float* watt;     // n, attraction weight a_i (edge force scaled by a_i a_j)
     float* vwr;            // n, r_i in the cell-sorted order (written by the sort) or nullptr
+    // nodes of degree > kHeavyDegree, whose attraction one warp sums (the others: a thread)
+    const int* heavy;
+    int n_heavy;
     DevState* st;
     const DevParams* prm;
     // FFT path

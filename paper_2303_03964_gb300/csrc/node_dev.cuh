@@ -64,10 +64,11 @@ __device__ __forceinline__ float rcp_fast(float x) {
     return r;
 }
 
-// With local-refinement weights wa (nullptr: all 1) the edge (i, j) is scaled by a_i a_j.
-__device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
-                                             const int* __restrict__ col, const float2* __restrict__ xy,
-                                             float alpha, float beta, const float* __restrict__ wa) {
+// With local-refinement weights (W, wa) the edge (i, j) is scaled by a_i a_j.
+template <bool W>
+__device__ __forceinline__ float2 attraction_t(int i, float2 p, const int* __restrict__ rowptr,
+                                               const int* __restrict__ col, const float2* __restrict__ xy,
+                                               float alpha, float beta, const float* __restrict__ wa) {
     float fx = 0.0f, fy = 0.0f;
     int e = rowptr[i];
     const int e1 = rowptr[i + 1];
@@ -79,15 +80,11 @@ __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restr
         for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + u);
 #pragma unroll
         for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
-        float wj[4] = {1.0f, 1.0f, 1.0f, 1.0f};
-        if (wa) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) wj[u] = __ldg(wa + j[u]);
-        }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const float dx = q[u].x - p.x, dy = q[u].y - p.y;
-            const float c = wj[u] * fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            if (W) c *= __ldg(wa + j[u]);
             fx = fmaf(c, dx, fx);
             fy = fmaf(c, dy, fy);
         }
@@ -96,11 +93,63 @@ __device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restr
         const int j = __ldg(col + e);
         const float2 q = xy[j];
         const float dx = q.x - p.x, dy = q.y - p.y;
-        const float c = (wa ? __ldg(wa + j) : 1.0f) * fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+        float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+        if (W) c *= __ldg(wa + j);
         fx = fmaf(c, dx, fx);
         fy = fmaf(c, dy, fy);
     }
-    const float s = wa ? alpha * __ldg(wa + i) : alpha;
+    const float s = W ? alpha * __ldg(wa + i) : alpha;
+    return make_float2(s * fx, s * fy);
+}
+
+__device__ __forceinline__ float2 attraction(int i, float2 p, const int* __restrict__ rowptr,
+                                             const int* __restrict__ col, const float2* __restrict__ xy,
+                                             float alpha, float beta, const float* __restrict__ wa) {
+    return wa ? attraction_t<true>(i, p, rowptr, col, xy, alpha, beta, wa)
+              : attraction_t<false>(i, p, rowptr, col, xy, alpha, beta, nullptr);
+}
+
+// The same sum for one node by the 32 lanes of a warp: lane l takes neighbours l, l + 32,
+// ... (four per round), then a fixed butterfly adds the lanes, so the result does not
+// depend on scheduling. All lanes return the sum.
+template <bool W>
+__device__ __forceinline__ float2 attraction_warp(int i, float2 p, const int* __restrict__ rowptr,
+                                                  const int* __restrict__ col, const float2* __restrict__ xy,
+                                                  float alpha, float beta, const float* __restrict__ wa, int lane) {
+    float fx = 0.0f, fy = 0.0f;
+    int e = rowptr[i] + lane;
+    const int e1 = rowptr[i + 1];
+    for (; e + 96 < e1; e += 128) {
+        int j[4];
+        float2 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) j[u] = __ldg(col + e + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = xy[j[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float dx = q[u].x - p.x, dy = q[u].y - p.y;
+            float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+            if (W) c *= __ldg(wa + j[u]);
+            fx = fmaf(c, dx, fx);
+            fy = fmaf(c, dy, fy);
+        }
+    }
+    for (; e < e1; e += 32) {
+        const int j = __ldg(col + e);
+        const float2 q = xy[j];
+        const float dx = q.x - p.x, dy = q.y - p.y;
+        float c = fmaf(beta, rcp_fast(1.0f + (dx * dx + dy * dy)), 1.0f);
+        if (W) c *= __ldg(wa + j);
+        fx = fmaf(c, dx, fx);
+        fy = fmaf(c, dy, fy);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    }
+    const float s = W ? alpha * __ldg(wa + i) : alpha;
     return make_float2(s * fx, s * fy);
 }
 
@@ -236,6 +285,80 @@ __device__ __forceinline__ void spread_box(const float2* __restrict__ sxy, const
             gin[plane + q] = ll2f_rn(mx[ly][lx]) * hs;
             gin[2 * plane + q] = ll2f_rn(my[ly][lx]) * hs;
         }
+}
+
+// spread_box shared by the L lanes of an aligned lane group (gmask), for grids with few
+// boxes (one thread per box would leave most of the GPU idle): lane g takes the nodes
+// s0 + g, s0 + g + L, ... and the lanes' int64 sums are combined by an xor butterfly.
+// The sums are exact, so the result is bit for bit that of spread_box.
+template <int K, int L>
+__device__ __forceinline__ void spread_box_group(const float2* __restrict__ sxy, const float* __restrict__ vw,
+                                                 int s0, int s1, int bx, int by, int g, unsigned gmask,
+                                                 const AxisGeom& ag, float* __restrict__ gin, int Gs) {
+    const size_t plane = (size_t)Gs * Gs;
+    long long acc[3][K][K];  // rho, m^x, m^y in fixed point; moments in units of h
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) acc[c][ly][lx] = 0;
+    const float inv_h = 1.0f / ag.h_hi;
+    for (int s = s0 + g; s < s1; s += 2 * L) {
+        const bool two = s + L < s1;
+        float2 pp[2];
+        float rr[2] = {ag.q_scale, ag.q_scale};
+        pp[0] = sxy[s];
+        pp[1] = two ? sxy[s + L] : pp[0];
+        if (vw) {
+            rr[0] *= vw[s];
+            rr[1] *= two ? vw[s + L] : 1.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+            const float ox = box_offset_at(pp[u].x, bx, ag);
+            const float oy = box_offset_at(pp[u].y, by, ag);
+            float wx[K], wy[K], dx[K], dy[K];
+            lagrange<K>(ox * inv_h, wx);
+            lagrange<K>(oy * inv_h, wy);
+#pragma unroll
+            for (int l = 0; l < K; ++l) {
+                dx[l] = (ox - ((float)l + 0.5f) * ag.hk) * inv_h;
+                dy[l] = (oy - ((float)l + 0.5f) * ag.hk) * inv_h;
+                wy[l] *= rr[u];
+            }
+#pragma unroll
+            for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+                for (int lx = 0; lx < K; ++lx) {
+                    const float w = wx[lx] * wy[ly];
+                    acc[0][ly][lx] += spread_q(w);
+                    acc[1][ly][lx] += spread_q(w * dx[lx]);
+                    acc[2][ly][lx] += spread_q(w * dy[ly]);
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+                for (int lx = 0; lx < K; ++lx) acc[c][ly][lx] += __shfl_xor_sync(gmask, acc[c][ly][lx], o);
+    // every lane holds the totals; lane g stores the entries v = g, g + L, ...
+    const float hs = ag.h_hi * ag.q_inv;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int ly = 0; ly < K; ++ly)
+#pragma unroll
+            for (int lx = 0; lx < K; ++lx) {
+                if (((c * K + ly) * K + lx) % L != g) continue;
+                const size_t q = (size_t)(by * K + ly) * Gs + (bx * K + lx);
+                gin[c * plane + q] = ll2f_rn(acc[c][ly][lx]) * (c == 0 ? ag.q_inv : hs);
+            }
 }
 
 // Back-projection (Sec. 3.4 step 3) at position p from the grid (A, O^x, O^y, 0):

@@ -331,25 +331,66 @@ __global__ void __launch_bounds__(kNodeThreads, 3) k_spread(NodeLaunch a) {
     }
 }
 
+// L lanes per box (grids with few boxes). blockDim is a multiple of L, so a lane's place
+// in its group is fixed across the grid-stride loop and a whole group passes or fails
+// the loop test together (same box).
+template <int K, int L>
+__global__ void __launch_bounds__(kNodeThreads, 3) k_spread_group(NodeLaunch a) {
+    pdl_wait();
+    pdl_trigger();
+    const GridDesc g = a.st->grid;
+    const int nbox = g.n_int * g.n_int;
+    const AxisGeom ag = axis_geom(g);
+    const float2* __restrict__ sxy = a.vxy[(int)(a.st->t_cur & 1) ^ 1];
+    const int gl = threadIdx.x & (L - 1);
+    const unsigned gmask = ((L == 32) ? 0xffffffffu : ((1u << L) - 1u)) << ((threadIdx.x & 31) & ~(L - 1));
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < L * nbox; q += gridDim.x * blockDim.x) {
+        const int b = q / L;
+        const int by = b / g.n_int;
+        const int bx = b - by * g.n_int;
+        spread_box_group<K, L>(sxy, a.vwr, max(a.off[b], 0), min(a.off[b + 1], a.n), bx, by, gl, gmask, ag, a.gin,
+                               a.Gs);
+    }
+}
+
 // ---------------------------------------------------------------- FFT path: attraction
 // fatt(i) in caller order (coalesced CSR rows); independent of the grid, so it runs
 // on a second stream while the sort, spread and FFT run.
-__global__ void __launch_bounds__(kNodeThreads) k_attract(NodeLaunch a) {
+// Blocks [0, heavy_blocks): one warp per node of degree > kHeavyDegree (listed in
+// a.heavy), launched first so that the long lists start early. The other blocks: one
+// thread per node (two per round), skipping the heavy ones.
+template <bool W>
+__global__ void __launch_bounds__(kNodeThreads) k_attract(NodeLaunch a, int heavy_blocks) {
     const int cur = (int)(a.st->t_cur & 1);  // set by k_grid, which precedes the fork
     const float2* __restrict__ xin = a.xy[cur];
     const float alpha = (float)a.prm->alpha, beta = (float)a.prm->beta;
-    const int stride = 2 * gridDim.x * blockDim.x;
-    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+    if ((int)blockIdx.x < heavy_blocks) {
+        const int w = blockIdx.x * (kNodeThreads / 32) + (threadIdx.x >> 5);
+        if (w >= a.n_heavy) return;  // whole warps leave together
+        const int i = a.heavy[w];
+        const float2 f = attraction_warp<W>(i, xin[i], a.rowptr, a.col, xin, alpha, beta, a.watt, threadIdx.x & 31);
+        if ((threadIdx.x & 31) == 0) a.fatt_out[i] = f;
+        return;
+    }
+    const int nb = gridDim.x - heavy_blocks, bx = blockIdx.x - heavy_blocks;
+    const int stride = 2 * nb * blockDim.x;
+    for (int base = 2 * bx * blockDim.x + threadIdx.x; base < a.n; base += stride) {
         const int ii[2] = {base, base + (int)blockDim.x};
         float2 pp[2], fa[2];
+        bool own[2];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) pp[u] = xin[ii[u] < a.n ? ii[u] : base];
+        for (int u = 0; u < 2; ++u) {
+            const int i = ii[u] < a.n ? ii[u] : base;
+            own[u] = ii[u] < a.n && a.rowptr[i + 1] - a.rowptr[i] <= kHeavyDegree;
+            pp[u] = xin[i];
+        }
 #pragma unroll
         for (int u = 0; u < 2; ++u)
-            fa[u] = attraction(ii[u] < a.n ? ii[u] : base, pp[u], a.rowptr, a.col, xin, alpha, beta, a.watt);
+            fa[u] = own[u] ? attraction_t<W>(ii[u], pp[u], a.rowptr, a.col, xin, alpha, beta, a.watt)
+                           : make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int u = 0; u < 2; ++u)
-            if (ii[u] < a.n) a.fatt_out[ii[u]] = fa[u];
+            if (own[u]) a.fatt_out[ii[u]] = fa[u];
     }
 }
 
@@ -613,19 +654,43 @@ cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     return e;
 }
 
+// Lanes per box: the smallest power of two (<= 16) that gives one wave of threads
+// (152 SMs x 3 CTAs x 256) over the largest box count; 1 for well-filled grids.
+int spread_lanes(int nbox_max) {
+    const long long wave = 152LL * 3 * kNodeThreads;
+    int L = 1;
+    while (L < 16 && (long long)L * nbox_max < wave) L <<= 1;
+    return L;
+}
+
+template <int K>
+static cudaError_t launch_spread_k(const NodeLaunch& a, cudaStream_t s) {
+    const int L = spread_lanes(a.nbox_max);
+    const int bb = blocks_for((long long)L * a.nbox_max, kNodeThreads);
+    switch (L) {
+        case 1: return launch_pdl(k_spread<K>, bb, kNodeThreads, 0, s, a);
+        case 2: return launch_pdl(k_spread_group<K, 2>, bb, kNodeThreads, 0, s, a);
+        case 4: return launch_pdl(k_spread_group<K, 4>, bb, kNodeThreads, 0, s, a);
+        case 8: return launch_pdl(k_spread_group<K, 8>, bb, kNodeThreads, 0, s, a);
+        default: return launch_pdl(k_spread_group<K, 16>, bb, kNodeThreads, 0, s, a);
+    }
+}
+
 cudaError_t launch_fft_spread(const NodeLaunch& a, cudaStream_t s) {
-    const int bb = blocks_for(a.nbox_max, kNodeThreads);
     switch (a.k) {
-        case 1: return launch_pdl(k_spread<1>, bb, kNodeThreads, 0, s, a);
-        case 2: return launch_pdl(k_spread<2>, bb, kNodeThreads, 0, s, a);
-        case 3: return launch_pdl(k_spread<3>, bb, kNodeThreads, 0, s, a);
+        case 1: return launch_spread_k<1>(a, s);
+        case 2: return launch_spread_k<2>(a, s);
+        case 3: return launch_spread_k<3>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_attract(const NodeLaunch& a, cudaStream_t s) {
     if (a.n == 0) return cudaSuccess;
-    k_attract<<<blocks_for(a.n, 2 * kNodeThreads), kNodeThreads, 0, s>>>(a);
+    const int heavy_blocks = (a.n_heavy + kNodeThreads / 32 - 1) / (kNodeThreads / 32);
+    const int blocks = heavy_blocks + blocks_for(a.n, 2 * kNodeThreads);
+    if (a.watt) k_attract<true><<<blocks, kNodeThreads, 0, s>>>(a, heavy_blocks);
+    else k_attract<false><<<blocks, kNodeThreads, 0, s>>>(a, heavy_blocks);
     return cudaGetLastError();
 }
 

@@ -109,6 +109,8 @@ struct tfdp_graph {
     float* watt = nullptr;
     float* vwr = nullptr;
     bool use_wrep = false, use_watt = false;
+    int* heavy = nullptr;  // nodes of degree > kHeavyDegree
+    int n_heavy = 0;
     int spread_shift = 0;  // fixed-point scale of the spread: 2^(27 - spread_shift)
     float* gin = nullptr;
     float2* T1 = nullptr;
@@ -153,6 +155,8 @@ struct tfdp_graph {
         a.wrep = use_wrep ? wrep : nullptr;
         a.watt = use_watt ? watt : nullptr;
         a.vwr = (use_wrep && params.rep_mode == TFDP_REP_FFT) ? vwr : nullptr;
+        a.heavy = heavy;
+        a.n_heavy = n_heavy;
         a.st = dst;
         a.prm = dprm;
         a.nbox_max = nbox_max;
@@ -383,11 +387,17 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval, i
         if (e == cudaSuccess) e = cudaEventRecordWithFlags(ev, g->time_stream, cudaEventRecordExternal);
         return e;
     };
+    // the attraction runs alone on the side stream: its events go on that stream itself,
+    // so that the timing branch of the main chain never waits for it
     auto begin = [&](int stage, cudaStream_t st) -> cudaError_t {
-        return ((tm >> stage) & 1u) ? stamp(g->ev_b[stage], g->time_fork[2 * stage], st) : cudaSuccess;
+        if (!((tm >> stage) & 1u)) return cudaSuccess;
+        if (stage == TFDP_STAGE_ATTRACT) return cudaEventRecordWithFlags(g->ev_b[stage], st, cudaEventRecordExternal);
+        return stamp(g->ev_b[stage], g->time_fork[2 * stage], st);
     };
     auto end = [&](int stage, cudaStream_t st) -> cudaError_t {
-        return ((tm >> stage) & 1u) ? stamp(g->ev_e[stage], g->time_fork[2 * stage + 1], st) : cudaSuccess;
+        if (!((tm >> stage) & 1u)) return cudaSuccess;
+        if (stage == TFDP_STAGE_ATTRACT) return cudaEventRecordWithFlags(g->ev_e[stage], st, cudaEventRecordExternal);
+        return stamp(g->ev_e[stage], g->time_fork[2 * stage + 1], st);
     };
     if (g->params.rep_mode == TFDP_REP_EXACT) {
         CK(begin(TFDP_STAGE_EXACT, s));
@@ -586,6 +596,9 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
         col[(size_t)fill[(size_t)b]++] = a;
     }
     for (int64_t i = 0; i < n; ++i) std::sort(col.begin() + rowptr[(size_t)i], col.begin() + rowptr[(size_t)i + 1]);
+    std::vector<int> heavy;  // nodes whose attraction a warp sums
+    for (int64_t i = 0; i < n; ++i)
+        if (deg[(size_t)i] > kHeavyDegree) heavy.push_back((int)i);
 
     tfdp_graph* g = new (std::nothrow) tfdp_graph();
     if (!g) return TFDP_ERR_OUT_OF_MEMORY;
@@ -617,6 +630,7 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     size_t o_xy1 = A.take(sizeof(float2) * nn);
     size_t o_rp = A.take(sizeof(int) * (nn + 1));
     size_t o_col = A.take(sizeof(int) * (size_t)std::max<int64_t>(2 * m, 1));
+    size_t o_heavy = A.take(sizeof(int) * std::max<size_t>(heavy.size(), 1));
     size_t o_part = A.take(sizeof(float2) * nn * (size_t)g->nchunks);
     size_t o_fr = A.take(sizeof(float2) * nn);
     size_t o_fa = A.take(sizeof(float2) * nn);
@@ -636,6 +650,8 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     g->xy[1] = (float2*)(b + o_xy1);
     g->rowptr = (int*)(b + o_rp);
     g->col = (int*)(b + o_col);
+    g->heavy = (int*)(b + o_heavy);
+    g->n_heavy = (int)heavy.size();
     g->part = (float2*)(b + o_part);
     g->frep_buf = (float2*)(b + o_fr);
     g->fatt_buf = (float2*)(b + o_fa);
@@ -667,6 +683,9 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     }
     if (m > 0 && (e = cudaMemcpyAsync(g->col, col.data(), sizeof(int) * (size_t)(2 * m), cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
         return fail(cuda_fail(e, "copy col"));
+    if (!heavy.empty() && (e = cudaMemcpyAsync(g->heavy, heavy.data(), sizeof(int) * heavy.size(),
+                                               cudaMemcpyHostToDevice, g->stream)) != cudaSuccess)
+        return fail(cuda_fail(e, "copy heavy list"));
     if (p.rep_mode == TFDP_REP_FFT) {
         st = alloc_fft(g);
         if (st != TFDP_OK) return fail(st);
@@ -906,6 +925,7 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
     const int nchunks = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
     size_t b = 0;
     b += sizeof(float2) * nn * (4 + (size_t)nchunks) + sizeof(int) * (nn + 1) + sizeof(int) * (size_t)(2 * m);
+    b += sizeof(int) * (size_t)std::min<int64_t>((int64_t)nn, 2 * m / (kHeavyDegree + 1) + 1);  // hub list bound
     b += sizeof(DevParams) + sizeof(DevState) + sizeof(double) * (size_t)p.total_iters + 16 * 256;
     if (p.rep_mode == TFDP_REP_FFT) {
         int P, logP, G_max, nbox_max;
