@@ -208,6 +208,16 @@ tfdp_status tfdp_set_stage_timing(tfdp_graph* g, int enable);
  * TFDP_ERR_INVALID_ARG if timing is off. */
 tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages);
 
+/* Upload positions, run `iters` iterations and download the result in one call (the
+ * end-to-end form of tfdp_set_positions + tfdp_iterate + tfdp_get_positions, with one
+ * host synchronisation at the end).
+ *   xy_in   2n floats, caller order, host memory; NULL keeps the current positions
+ *   iters   >= 0 iterations (Sec. 3.1 loop with the step schedule of the parameters)
+ *   xy_out  2n floats, host memory, receives the positions after the iterations; may
+ *           equal xy_in. Page-locked (pinned) buffers make both copies DMA transfers.
+ * TFDP_ERR_INVALID_ARG for a NULL graph or xy_out, iters < 0. */
+tfdp_status tfdp_run(tfdp_graph* g, const float* xy_in, int32_t iters, float* xy_out);
+
 /* Local refinement (Sec. 5 "Local Refinement", fisheye views): per-node weights. The
  * repulsion between nodes i and j is scaled by w_rep[i] * w_rep[j] and the attraction
  * along edge (i, j) by w_att[i] * w_att[j]. The paper describes the effect (stronger

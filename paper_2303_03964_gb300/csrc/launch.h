@@ -86,6 +86,7 @@ struct NodeLaunch {
 cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s);
 // Visit order `slot` := caller order (identity permutation, positions xy[slot]).
 cudaError_t launch_order_reset(const NodeLaunch& a, int slot, cudaStream_t s);
+cudaError_t launch_order_refresh(const NodeLaunch& a, int slot, cudaStream_t s);
 // FFT path, first kernel of an iteration: grid policy, t_cur = iter, step, spectrum key.
 cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s);
 // FFT path, before the grid interaction: bin + scan + scatter (3 kernels), spread (1).

@@ -154,6 +154,16 @@ __global__ void __launch_bounds__(kNodeThreads) k_order_reset(NodeLaunch a, int 
     }
 }
 
+// Keep visit order `slot` (a permutation left by an earlier sort) and refresh its
+// positions from the caller-order ones: positions uploaded close to the previous ones
+// keep the next sort coherent.
+__global__ void __launch_bounds__(kNodeThreads) k_order_refresh(NodeLaunch a, int slot) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
+        const int i = a.vperm[slot][v];
+        a.vxy[slot][v] = ((unsigned)i < (unsigned)a.n) ? a.xy[slot][i] : make_float2(0.0f, 0.0f);
+    }
+}
+
 // ---------------------------------------------------------------- FFT path: scan
 // Single-pass exclusive scan of the box counts with decoupled look-back. Each CTA takes
 // a ticket; ticket order is launch order, so a CTA only waits for CTAs that are already
@@ -629,6 +639,12 @@ static inline int blocks_for(long long work, int threads) {
 cudaError_t launch_order_reset(const NodeLaunch& a, int slot, cudaStream_t s) {
     if (a.n == 0 || !a.vperm[slot]) return cudaSuccess;
     k_order_reset<<<blocks_for(a.n, kNodeThreads), kNodeThreads, 0, s>>>(a, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_order_refresh(const NodeLaunch& a, int slot, cudaStream_t s) {
+    if (a.n == 0 || !a.vperm[slot]) return cudaSuccess;
+    k_order_refresh<<<blocks_for(a.n, kNodeThreads), kNodeThreads, 0, s>>>(a, slot);
     return cudaGetLastError();
 }
 

@@ -104,6 +104,7 @@ struct tfdp_graph {
     int* vperm[2] = {nullptr, nullptr};
     float2* vxy[2] = {nullptr, nullptr};
     bool last_was_eval = false;  // which visit-order buffer holds the latest sort
+    bool order_valid[2] = {false, false};  // vperm[slot] holds a permutation from a sort / reset
     // local refinement: per-node weights (caller order) and r_i in sorted order
     float* wrep = nullptr;
     float* watt = nullptr;
@@ -289,6 +290,7 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fft arena)");
     char* b = (char*)mem;
     g->fft_mem = mem;
+    g->order_valid[0] = g->order_valid[1] = false;  // the visit orders of a new arena are unset
     g->cnt = (int*)(b + o_cnt);
     g->off = (int*)(b + o_off);
     g->bsum = (int*)(b + o_bsum);
@@ -362,12 +364,20 @@ tfdp_status upload_params(tfdp_graph* g) {
 // Recompute the bbox slot of the current positions.
 tfdp_status refresh_bbox(tfdp_graph* g) {
     const int slot = (int)(g->host_iter & 1);
-    const unsigned init[2] = {kOrdMinInit, kOrdMaxInit};
-    CK(cudaMemcpyAsync(&g->dst->bbox[slot][0], init, sizeof(init), cudaMemcpyHostToDevice, g->stream));
-    CK(cudaStreamSynchronize(g->stream));  // `init` is a stack buffer
+    static_assert(kOrdMinInit == 0xFFFFFFFFu && kOrdMaxInit == 0u, "bbox identities set by memset");
+    CK(cudaMemsetAsync(&g->dst->bbox[slot][0], 0xFF, sizeof(unsigned), g->stream));
+    CK(cudaMemsetAsync(&g->dst->bbox[slot][1], 0x00, sizeof(unsigned), g->stream));
     CK(launch_bbox(g->node_launch(), slot, g->stream));
-    // the caller order is the visit order after an upload (the FFT path only)
-    if (g->fft_mem && g->params.rep_mode == TFDP_REP_FFT) CK(launch_order_reset(g->node_launch(), slot, g->stream));
+    // visit order after an upload (FFT path): the last sorted order with the new
+    // positions when there is one (keeps the next sort coherent), else the caller order
+    if (g->fft_mem && g->params.rep_mode == TFDP_REP_FFT) {
+        if (g->order_valid[slot]) {
+            CK(launch_order_refresh(g->node_launch(), slot, g->stream));
+        } else {
+            CK(launch_order_reset(g->node_launch(), slot, g->stream));
+            g->order_valid[slot] = true;
+        }
+    }
     return TFDP_OK;
 }
 
@@ -707,8 +717,10 @@ tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
         void* before = g->fft_mem;
         st = alloc_fft(g);
         if (st != TFDP_OK) return st;
-        if ((to_fft || g->fft_mem != before) && g->n > 0)
+        if ((to_fft || g->fft_mem != before) && g->n > 0) {
             CK(launch_order_reset(g->node_launch(), (int)(g->host_iter & 1), g->stream));
+            g->order_valid[g->host_iter & 1] = true;
+        }
     }
     st = upload_params(g);
     if (st != TFDP_OK) return st;
@@ -768,6 +780,24 @@ tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
         left -= seg;
     }
     g->last_was_eval = false;
+    g->order_valid[0] = g->order_valid[1] = true;  // the sorts wrote both visit orders
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_run(tfdp_graph* g, const float* xy_in, int32_t iters, float* xy_out) {
+    if (!g || (!xy_out && g->n > 0) || iters < 0) return TFDP_ERR_INVALID_ARG;
+    if (g->n == 0) return tfdp_iterate(g, iters);
+    if (xy_in) {
+        const int slot = (int)(g->host_iter & 1);
+        CK(cudaMemcpyAsync(g->xy[slot], xy_in, sizeof(float2) * (size_t)g->n, cudaMemcpyHostToDevice, g->stream));
+        tfdp_status st = refresh_bbox(g);  // stream-ordered, no synchronisation
+        if (st != TFDP_OK) return st;
+    }
+    tfdp_status st = tfdp_iterate(g, iters);
+    if (st != TFDP_OK) return st;
+    const int slot = (int)(g->host_iter & 1);
+    CK(cudaMemcpyAsync(xy_out, g->xy[slot], sizeof(float2) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
     return TFDP_OK;
 }
 
@@ -791,6 +821,7 @@ tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_dev
     tfdp_status st = enqueue_step(g, g->stream, 0, 1, g->k_now());
     if (st != TFDP_OK) return st;
     g->last_was_eval = true;
+    g->order_valid[(g->host_iter & 1) ^ 1] = true;  // its sort wrote the other visit order
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (frep) CK(cudaMemcpyAsync(frep, g->frep_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
     if (fatt) CK(cudaMemcpyAsync(fatt, g->fatt_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));

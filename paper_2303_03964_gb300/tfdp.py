@@ -72,6 +72,7 @@ _SIGS = {
     "tfdp_get_params": ([_p, ctypes.POINTER(Params)], ctypes.c_int),
     "tfdp_set_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
     "tfdp_set_node_weights": ([_p, _p, _p, ctypes.c_int], ctypes.c_int),
+    "tfdp_run": ([_p, _p, ctypes.c_int32, _p], ctypes.c_int),
     "tfdp_get_positions": ([_p, _p, ctypes.c_int], ctypes.c_int),
     "tfdp_iterate": ([_p, ctypes.c_int32], ctypes.c_int),
     "tfdp_set_iteration": ([_p, ctypes.c_int64], ctypes.c_int),
@@ -245,6 +246,15 @@ class Graph:
         return a
 
     # ------------------------------------------------------------ compute
+    def run(self, xy_in, iters, xy_out):
+        """Upload `xy_in` (host, (n, 2) float32; None keeps the positions), run `iters`
+        iterations and download into `xy_out` (host, (n, 2) float32) in one call."""
+        src = None if xy_in is None else _host_f32(xy_in, self.n)  # kept alive across the call
+        pin = None if src is None else src.ctypes.data_as(_p)
+        assert xy_out.dtype == np.float32 and xy_out.flags.c_contiguous and xy_out.size == 2 * self.n
+        _check(lib.tfdp_run(self._h, pin, int(iters), xy_out.ctypes.data_as(_p)), "tfdp_run")
+        return xy_out
+
     def iterate(self, iters=1):
         _check(lib.tfdp_iterate(self._h, int(iters)), "tfdp_iterate")
 

@@ -388,3 +388,45 @@ def test_dynamic_k_forces_in_each_phase(tfdp, t):
     assert st["grid_k"] == k
     _, ref = _oracle_fft(xy, st, 2.0, k, 255, 1)
     assert record("fft_dynk_forces_t%d_k%d" % (t, k), rel_l2(fr, ref)) <= FORCE_TOL
+
+
+def test_upload_after_iterations_keeps_the_forces_exact(tfdp):
+    """After iterations both visit orders hold sorted permutations; an upload keeps the
+    current one and refreshes its positions. Forces at unrelated new positions must still
+    equal the oracle's, and a second upload of the same positions must give the same bits."""
+    n, e, xy = _sbm20k(23)
+    rng = np.random.default_rng(24)
+    new = rng.uniform(-90, 60, size=(n, 2)).astype(np.float32)
+    with tfdp.Graph(n, e, xy, _params(tfdp, grid_max=255)) as g:
+        g.iterate(5)
+        g.set_positions(new)
+        fr, fa = g.eval_forces()
+        st = g.stats()
+        g.set_positions(new)
+        fr2, _ = g.eval_forces()
+    _, ref = _oracle_fft(new, st, 2.0, 3, 255, 1)
+    assert record("fft_upload_after_iterations", rel_l2(fr, ref)) <= FORCE_TOL
+    assert rel_l2(fa, oracle.attraction(e, new.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
+    assert np.array_equal(fr, fr2)
+
+
+def test_run_equals_upload_iterate_download(tfdp):
+    """tfdp_run (one call, one synchronisation) gives the bits of set_positions +
+    iterate + get_positions, including a call that keeps the positions (NULL input)."""
+    n, e, xy = _sbm20k(25)
+    new = np.random.default_rng(26).uniform(-70, 70, size=(n, 2)).astype(np.float32)
+    outs = []
+    for fused in (False, True):
+        with tfdp.Graph(n, e, xy, _params(tfdp, grid_max=255)) as g:
+            g.iterate(3)
+            if fused:
+                a = g.run(new, 4, np.empty((n, 2), np.float32))
+                b = g.run(None, 2, np.empty((n, 2), np.float32))
+            else:
+                g.set_positions(new)
+                g.iterate(4)
+                a = g.get_positions()
+                g.iterate(2)
+                b = g.get_positions()
+            outs.append((a, b))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
