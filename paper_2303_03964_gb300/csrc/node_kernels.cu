@@ -670,12 +670,12 @@ cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     return e;
 }
 
-// Lanes per box: the smallest power of two (<= 16) that gives one wave of threads
+// Lanes per box: the smallest power of two (<= 16) that gives half a wave of threads
 // (152 SMs x 3 CTAs x 256) over the largest box count; 1 for well-filled grids.
 int spread_lanes(int nbox_max) {
     const long long wave = 152LL * 3 * kNodeThreads;
     int L = 1;
-    while (L < 16 && (long long)L * nbox_max < wave) L <<= 1;
+    while (L < 16 && 2LL * L * nbox_max < wave) L <<= 1;  // half a wave is enough
     return L;
 }
 
