@@ -10,7 +10,8 @@
 // (node_dev.cuh, fft_stages.cuh), so every graph evolves as it would alone.
 //
 // All graphs of a batch share k and the FFT size P (the largest any graph needs:
-// P >= 2 G_max - 1 for every graph, so each graph's linear convolution is exact).
+// P >= 2 G_max - 1 for every graph, so each graph's linear convolution is exact). The
+// kernel itself is in batch_kernel.cuh.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -23,318 +24,12 @@
 #include <vector>
 
 #include "../../include/tfdp.h"
-#include "common.cuh"
-#include "fft_stages.cuh"
-#include "node_dev.cuh"
+#include "batch_kernel.cuh"
 
-namespace cg = cooperative_groups;
 using namespace tfdp;
+using namespace tfdp::bk;
 
 namespace {
-
-constexpr int kBThreads = 256;   // threads per CTA in every phase
-constexpr int kBChunk = 256;     // nodes / boxes per work item
-
-// Per-graph geometry and buffers (device copy).
-struct BGraph {
-    int n, node_off, rowptr_off, col_off;
-    int G_max, Gs, ystride, nbox_max;
-    int* cnt;
-    int* off;
-    float* gin;
-    float2* T1;
-    float2* T2;
-    float4* gout;
-    float2* S1;
-    float* specK;
-    float* specHx;
-    float* specHy;
-};
-
-struct BatchArgs {
-    int B;
-    const BGraph* graphs;
-    DevState* st;           // [B]
-    const DevParams* prm;   // [B]
-    float2* xy[2];          // packed caller-order positions (global node index)
-    float2* vxy[2];         // packed visit orders (see launch.h NodeLaunch)
-    int* vperm[2];          // global node ids
-    int2* keyslot;
-    float2* fatt;
-    float2* frep;
-    const int* rowptr;      // per graph n + 1 entries (local offsets into its col range)
-    const int* col;         // global node ids
-    const float2* tw;
-    const int* pre_nodes;   // [B + 1] prefix of node chunks
-    const int* pre_boxes;   // [B + 1] prefix of box chunks (nbox_max)
-    const int* pre_rows;    // [B + 1] prefix of row blocks (data + spectrum)
-    const int* pre_cols;    // [B + 1] prefix of column blocks
-    int iters;
-    int advance;
-    int eval;
-};
-
-// graph owning global item `it` of a phase with prefix table pre[0..B]
-__device__ __forceinline__ int owner(const int* __restrict__ pre, int B, int it) {
-    int lo = 0, hi = B;  // pre[lo] <= it < pre[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(pre + mid) <= it) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
-template <int LOGP, int K>
-__global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
-    using Rg = RegGeom<LOGP>;
-    extern __shared__ float2 sm[];
-    cg::grid_group grid = cg::this_grid();
-    const int lane = threadIdx.x & 31;
-    for (int it = 0; it < a.iters; ++it) {
-        // ---- phase 0: grid policy, step and spectrum key of every graph
-        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.B; g += gridDim.x * blockDim.x)
-            grid_decide(a.st + g, a.prm[g], a.advance);
-        grid.sync();
-
-        // ---- phase 1: binning (visit order) and attraction (caller order)
-        const int n_node_items = __ldg(a.pre_nodes + a.B);
-        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
-            const int g = owner(a.pre_nodes, a.B, item);
-            const BGraph G = a.graphs[g];
-            const DevState* st = a.st + g;
-            const int cur = (int)(st->t_cur & 1);
-            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
-            if (v < G.n) {
-                const int gv = G.node_off + v;
-                const float2 p = a.vxy[cur][gv];
-                float tq;
-                const int bx = box_of(p.x, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
-                const int by = box_of(p.y, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
-                const int key = by * st->grid.n_int + bx;
-                const unsigned active = __activemask();
-                const unsigned same = __match_any_sync(active, key);
-                const int leader = __ffs(same) - 1;
-                int base = 0;
-                if (lane == leader) base = atomicAdd(G.cnt + key, __popc(same));
-                base = __shfl_sync(same, base, leader);
-                a.keyslot[gv] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
-                // attraction of caller-order node gv (rowptr holds local offsets)
-                const float2 pi = a.xy[cur][gv];
-                a.fatt[gv] = attraction(v, pi, a.rowptr + G.rowptr_off, a.col + G.col_off, a.xy[cur],
-                                        (float)a.prm[g].alpha, (float)a.prm[g].beta, nullptr);
-            }
-        }
-        grid.sync();
-
-        // ---- phase 2: exclusive scan of each graph's box counts (one CTA per graph)
-        for (int g = blockIdx.x; g < a.B; g += gridDim.x) {
-            const BGraph G = a.graphs[g];
-            const int nbox = a.st[g].grid.n_int * a.st[g].grid.n_int;
-            __shared__ int s_w[32];
-            __shared__ int s_carry;
-            if (threadIdx.x == 0) s_carry = 0;
-            __syncthreads();
-            for (int c0 = 0; c0 < nbox; c0 += kBThreads * 8) {
-                const int i0 = c0 + threadIdx.x * 8;
-                int v[8], tsum = 0;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    v[q] = (i0 + q < nbox) ? G.cnt[i0 + q] : 0;
-                    tsum += v[q];
-                }
-                int incl = tsum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                const int w = threadIdx.x >> 5;
-                if (lane == 31) s_w[w] = incl;
-                __syncthreads();
-                if (w == 0) {
-                    const int x = lane < (kBThreads >> 5) ? s_w[lane] : 0;
-                    int xi = x;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xffffffffu, xi, o);
-                        if (lane >= o) xi += y;
-                    }
-                    if (lane < (kBThreads >> 5)) s_w[lane] = xi - x;
-                }
-                __syncthreads();
-                int run = s_carry + s_w[w] + incl - tsum;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    if (i0 + q < nbox) {
-                        G.off[i0 + q] = run;
-                        G.cnt[i0 + q] = 0;
-                    }
-                    run += v[q];
-                }
-                __syncthreads();
-                if (threadIdx.x == kBThreads - 1) s_carry = run;
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) G.off[nbox] = G.n;
-            __syncthreads();
-        }
-        grid.sync();
-
-        // ---- phase 3: scatter into the new cell-sorted order
-        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
-            const int g = owner(a.pre_nodes, a.B, item);
-            const BGraph G = a.graphs[g];
-            DevState* st = a.st + g;
-            const int cur = (int)(st->t_cur & 1);
-            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
-            if (v < G.n) {
-                const int gv = G.node_off + v;
-                const int2 ks = a.keyslot[gv];
-                const int pos = G.off[ks.x] + ks.y;
-                const int i = a.vperm[cur][gv];
-                if ((unsigned)pos >= (unsigned)G.n || i < G.node_off || i >= G.node_off + G.n) {
-                    atomicOr(&st->flags, FLAG_SORT_RANGE);
-                } else {
-                    a.vxy[cur ^ 1][G.node_off + pos] = a.vxy[cur][gv];
-                    a.vperm[cur ^ 1][G.node_off + pos] = i;
-                }
-            }
-        }
-        grid.sync();
-
-        // ---- phase 4: spread, one thread per box
-        const int n_box_items = __ldg(a.pre_boxes + a.B);
-        for (int item = blockIdx.x; item < n_box_items; item += gridDim.x) {
-            const int g = owner(a.pre_boxes, a.B, item);
-            const BGraph G = a.graphs[g];
-            const DevState* st = a.st + g;
-            const GridDesc gd = st->grid;
-            const int b = (item - __ldg(a.pre_boxes + g)) * kBChunk + threadIdx.x;
-            if (b < gd.n_int * gd.n_int) {
-                const int by = b / gd.n_int;
-                const int bx = b - by * gd.n_int;
-                const float2* sxy = a.vxy[(int)(st->t_cur & 1) ^ 1] + G.node_off;
-                spread_box<K>(sxy, nullptr, max(G.off[b], 0), min(G.off[b + 1], G.n), bx, by, axis_geom(gd), G.gin,
-                              G.Gs);
-            }
-        }
-        grid.sync();
-
-        // ---- phase 5: forward row transforms (and kernel-sample rows on a rebuild)
-        const int n_row_items = __ldg(a.pre_rows + a.B);
-        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
-            const int g = owner(a.pre_rows, a.B, item);
-            const BGraph G = a.graphs[g];
-            const DevState* st = a.st + g;
-            const int blk = item - __ldg(a.pre_rows + g);
-            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-            if (blk < data_blocks) {
-                GridSource gs;
-                gs.gin = G.gin;
-                gs.Gs = G.Gs;
-                rows_fwd_body<LOGP>(gs, st->grid.G, blk, G.T1, G.ystride, a.tw, sm);
-            } else if (st->spec_dirty) {
-                KernelSource ks;
-                ks.P = 1 << LOGP;
-                ks.bind(st, a.prm + g);
-                rows_fwd_body<LOGP>(ks, ks.P, blk - data_blocks, G.S1, 1 << LOGP, a.tw, sm);
-            }
-            __syncthreads();
-        }
-        grid.sync();
-
-        // ---- phase 6: column transforms, spectral product (spectrum rebuilt if needed)
-        const int n_col_items = __ldg(a.pre_cols + a.B);
-        for (int item = blockIdx.x; item < n_col_items; item += gridDim.x) {
-            const int g = owner(a.pre_cols, a.B, item);
-            const BGraph G = a.graphs[g];
-            const DevState* st = a.st + g;
-            cols_body<LOGP>(item - __ldg(a.pre_cols + g), G.T1, G.T2, G.ystride, G.specK, G.specHx, G.specHy, G.S1,
-                            a.tw, st->grid.G, st->spec_dirty, sm);
-            __syncthreads();
-        }
-        grid.sync();
-
-        // ---- phase 7: inverse row transforms into (A, O^x, O^y)
-        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
-            const int g = owner(a.pre_rows, a.B, item);
-            const BGraph G = a.graphs[g];
-            const int blk = item - __ldg(a.pre_rows + g);
-            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-            if (blk < data_blocks) rows_inv_body<LOGP>(blk, G.T2, G.ystride, G.gout, G.Gs, a.tw, a.st[g].grid.G, sm);
-            __syncthreads();
-        }
-        grid.sync();
-
-        // ---- phase 8: back-projection + update in sorted order
-        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
-            const int g = owner(a.pre_nodes, a.B, item);
-            const BGraph G = a.graphs[g];
-            DevState* st = a.st + g;
-            const int cur = (int)(st->t_cur & 1);
-            const int nxt = cur ^ 1;
-            const int chunk = item - __ldg(a.pre_nodes + g);
-            const int s = chunk * kBChunk + threadIdx.x;
-            float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
-            unsigned bad = 0;
-            if (s < G.n) {
-                const int gs = G.node_off + s;
-                const float2 p = a.vxy[nxt][gs];
-                const int i = a.vperm[nxt][gs];
-                if (i >= G.node_off && i < G.node_off + G.n) {
-                    const float2 fr = gather_frep<K>(p, axis_geom(st->grid), G.gout, G.Gs);
-                    sfx = fr.x;
-                    sfy = fr.y;
-                    if (a.eval) {
-                        a.frep[i] = fr;
-                    } else {
-                        const float2 fa = a.fatt[i];
-                        const float2 q = capped_step(p, make_float2(fr.x + fa.x, fr.y + fa.y), (float)st->step_cur);
-                        if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
-                        a.xy[nxt][i] = q;
-                        a.vxy[nxt][gs] = q;
-                        mn = fminf(q.x, q.y);
-                        mx = fmaxf(q.x, q.y);
-                    }
-                }
-            }
-            if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
-            // per-chunk reduction; every chunk lies inside one graph
-            __shared__ float s_mn[kBThreads / 32], s_mx[kBThreads / 32], s_fx[kBThreads / 32], s_fy[kBThreads / 32];
-            mn = warp_min(mn);
-            mx = warp_max(mx);
-            sfx = warp_sumf(sfx);
-            sfy = warp_sumf(sfy);
-            const int w = threadIdx.x >> 5;
-            if (lane == 0) {
-                s_mn[w] = mn;
-                s_mx[w] = mx;
-                s_fx[w] = sfx;
-                s_fy[w] = sfy;
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double fx = 0.0, fy = 0.0;
-                for (int q = 0; q < kBThreads / 32; ++q) {
-                    mn = fminf(mn, s_mn[q]);
-                    mx = fmaxf(mx, s_mx[q]);
-                    fx += s_fx[q];
-                    fy += s_fy[q];
-                }
-                if (!a.eval && mn <= mx) {
-                    atomicMin(&st->bbox[nxt][0], f2ord(mn));
-                    atomicMax(&st->bbox[nxt][1], f2ord(mx));
-                }
-                atomicAdd(&st->net_frep[0], fx);
-                atomicAdd(&st->net_frep[1], fy);
-                if (chunk == 0 && !a.eval && a.advance) st->iter = st->t_cur + 1;
-            }
-            __syncthreads();
-        }
-        grid.sync();
-    }
-}
 
 // Visit order := caller order for every graph (after a position upload).
 __global__ void k_batch_order_reset(int N, const float2* __restrict__ xy, float2* vxy, int* vperm) {
@@ -415,57 +110,22 @@ struct tfdp_batch {
 
 namespace {
 
-template <int LOGP, int K>
-cudaError_t batch_launch_t(const BatchArgs& a, int blocks, cudaStream_t s) {
-    using Rg = RegGeom<LOGP>;
-    const size_t smem = std::max(Rg::rows_smem, Rg::cols_smem);  // attribute set at creation
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(blocks);
-    cfg.blockDim = dim3(kBThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch<LOGP, K>, a);
-}
-
-template <int LOGP, int K>
-cudaError_t batch_occupancy_t(int* blocks_per_sm) {
-    using Rg = RegGeom<LOGP>;
-    const size_t smem = std::max(Rg::rows_smem, Rg::cols_smem);
-    cudaError_t e = cudaFuncSetAttribute(k_batch<LOGP, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<LOGP, K>, kBThreads, smem);
-}
-
-// RegGeom<LOGP>::T * CG must equal kBThreads for the FFT phases: P in [128, 2048].
-#define TFDP_BATCH_DISPATCH(FN, ...)                               \
-    switch (b->logP * 4 + b->k) {                                  \
-        case 7 * 4 + 1: return FN<7, 1>(__VA_ARGS__);              \
-        case 7 * 4 + 2: return FN<7, 2>(__VA_ARGS__);              \
-        case 7 * 4 + 3: return FN<7, 3>(__VA_ARGS__);              \
-        case 8 * 4 + 1: return FN<8, 1>(__VA_ARGS__);              \
-        case 8 * 4 + 2: return FN<8, 2>(__VA_ARGS__);              \
-        case 8 * 4 + 3: return FN<8, 3>(__VA_ARGS__);              \
-        case 9 * 4 + 1: return FN<9, 1>(__VA_ARGS__);              \
-        case 9 * 4 + 2: return FN<9, 2>(__VA_ARGS__);              \
-        case 9 * 4 + 3: return FN<9, 3>(__VA_ARGS__);              \
-        case 10 * 4 + 1: return FN<10, 1>(__VA_ARGS__);            \
-        case 10 * 4 + 2: return FN<10, 2>(__VA_ARGS__);            \
-        case 10 * 4 + 3: return FN<10, 3>(__VA_ARGS__);            \
-        case 11 * 4 + 1: return FN<11, 1>(__VA_ARGS__);            \
-        case 11 * 4 + 2: return FN<11, 2>(__VA_ARGS__);            \
-        case 11 * 4 + 3: return FN<11, 3>(__VA_ARGS__);            \
-        default: return cudaErrorInvalidValue;                     \
-    }
-
 cudaError_t batch_launch(const tfdp_batch* b, const BatchArgs& a, cudaStream_t s) {
-    TFDP_BATCH_DISPATCH(batch_launch_t, a, b->grid_blocks, s)
+    switch (b->k) {
+        case 1: return batch_launch_k<1>(b->logP, a, b->grid_blocks, s);
+        case 2: return batch_launch_k<2>(b->logP, a, b->grid_blocks, s);
+        case 3: return batch_launch_k<3>(b->logP, a, b->grid_blocks, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
-cudaError_t batch_occupancy(const tfdp_batch* b, int* bps) { TFDP_BATCH_DISPATCH(batch_occupancy_t, bps) }
+cudaError_t batch_occupancy(const tfdp_batch* b, int* bps) {
+    switch (b->k) {
+        case 1: return batch_occupancy_k<1>(b->logP, bps);
+        case 2: return batch_occupancy_k<2>(b->logP, bps);
+        case 3: return batch_occupancy_k<3>(b->logP, bps);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 tfdp_status upload_batch_params(tfdp_batch* b) {
     std::vector<DevParams> dp((size_t)b->B);

@@ -1,0 +1,388 @@
+// batch_kernel.cuh -- the cooperative persistent kernel of a batch of graphs and the
+// data it reads. The kernel is instantiated per k in batch_k1.cu, batch_k2.cu and
+// batch_k3.cu (which nvcc compiles in parallel); batch.cu holds the host side.
+//
+// One launch runs `iters` iterations of every graph: the nine phases of an iteration
+// (grid policy; binning + attraction; per-graph scan; scatter; spread; row / column /
+// inverse-row FFT stages; back-projection + update), each phase distributing
+// (graph, item) work over all CTAs, with a grid-wide barrier between phases. The
+// per-node and per-transform arithmetic is the single-graph code (node_dev.cuh,
+// fft_stages.cuh), so every graph evolves as it would alone.
+#pragma once
+
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "fft_stages.cuh"
+#include "node_dev.cuh"
+
+namespace tfdp {
+namespace bk {
+
+namespace cg = cooperative_groups;
+
+constexpr int kBThreads = 256;   // threads per CTA in every phase
+constexpr int kBChunk = 256;     // nodes / boxes per work item
+
+// Per-graph geometry and buffers (device copy).
+struct BGraph {
+    int n, node_off, rowptr_off, col_off;
+    int G_max, Gs, ystride, nbox_max;
+    int* cnt;
+    int* off;
+    float* gin;
+    float2* T1;
+    float2* T2;
+    float4* gout;
+    float2* S1;
+    float* specK;
+    float* specHx;
+    float* specHy;
+};
+
+struct BatchArgs {
+    int B;
+    const BGraph* graphs;
+    DevState* st;           // [B]
+    const DevParams* prm;   // [B]
+    float2* xy[2];          // packed caller-order positions (global node index)
+    float2* vxy[2];         // packed visit orders (see launch.h NodeLaunch)
+    int* vperm[2];          // global node ids
+    int2* keyslot;
+    float2* fatt;
+    float2* frep;
+    const int* rowptr;      // per graph n + 1 entries (local offsets into its col range)
+    const int* col;         // global node ids
+    const float2* tw;
+    const int* pre_nodes;   // [B + 1] prefix of node chunks
+    const int* pre_boxes;   // [B + 1] prefix of box chunks (nbox_max)
+    const int* pre_rows;    // [B + 1] prefix of row blocks (data + spectrum)
+    const int* pre_cols;    // [B + 1] prefix of column blocks
+    int iters;
+    int advance;
+    int eval;
+};
+
+// graph owning global item `it` of a phase with prefix table pre[0..B]
+__device__ __forceinline__ int owner(const int* __restrict__ pre, int B, int it) {
+    int lo = 0, hi = B;  // pre[lo] <= it < pre[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(pre + mid) <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int LOGP, int K>
+__global__ void __launch_bounds__(kBThreads, 2) k_batch(BatchArgs a) {
+    using Rg = RegGeom<LOGP>;
+    extern __shared__ float2 sm[];
+    cg::grid_group grid = cg::this_grid();
+    const int lane = threadIdx.x & 31;
+    for (int it = 0; it < a.iters; ++it) {
+        // ---- phase 0: grid policy, step and spectrum key of every graph
+        for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < a.B; g += gridDim.x * blockDim.x)
+            grid_decide(a.st + g, a.prm[g], a.advance);
+        grid.sync();
+
+        // ---- phase 1: binning (visit order) and attraction (caller order)
+        const int n_node_items = __ldg(a.pre_nodes + a.B);
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
+            if (v < G.n) {
+                const int gv = G.node_off + v;
+                const float2 p = a.vxy[cur][gv];
+                float tq;
+                const int bx = box_of(p.x, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
+                const int by = box_of(p.y, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
+                const int key = by * st->grid.n_int + bx;
+                const unsigned active = __activemask();
+                const unsigned same = __match_any_sync(active, key);
+                const int leader = __ffs(same) - 1;
+                int base = 0;
+                if (lane == leader) base = atomicAdd(G.cnt + key, __popc(same));
+                base = __shfl_sync(same, base, leader);
+                a.keyslot[gv] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
+                // attraction of caller-order node gv (rowptr holds local offsets)
+                const float2 pi = a.xy[cur][gv];
+                a.fatt[gv] = attraction(v, pi, a.rowptr + G.rowptr_off, a.col + G.col_off, a.xy[cur],
+                                        (float)a.prm[g].alpha, (float)a.prm[g].beta, nullptr);
+            }
+        }
+        grid.sync();
+
+        // ---- phase 2: exclusive scan of each graph's box counts (one CTA per graph)
+        for (int g = blockIdx.x; g < a.B; g += gridDim.x) {
+            const BGraph G = a.graphs[g];
+            const int nbox = a.st[g].grid.n_int * a.st[g].grid.n_int;
+            __shared__ int s_w[32];
+            __shared__ int s_carry;
+            if (threadIdx.x == 0) s_carry = 0;
+            __syncthreads();
+            for (int c0 = 0; c0 < nbox; c0 += kBThreads * 8) {
+                const int i0 = c0 + threadIdx.x * 8;
+                int v[8], tsum = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    v[q] = (i0 + q < nbox) ? G.cnt[i0 + q] : 0;
+                    tsum += v[q];
+                }
+                int incl = tsum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int w = threadIdx.x >> 5;
+                if (lane == 31) s_w[w] = incl;
+                __syncthreads();
+                if (w == 0) {
+                    const int x = lane < (kBThreads >> 5) ? s_w[lane] : 0;
+                    int xi = x;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xffffffffu, xi, o);
+                        if (lane >= o) xi += y;
+                    }
+                    if (lane < (kBThreads >> 5)) s_w[lane] = xi - x;
+                }
+                __syncthreads();
+                int run = s_carry + s_w[w] + incl - tsum;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (i0 + q < nbox) {
+                        G.off[i0 + q] = run;
+                        G.cnt[i0 + q] = 0;
+                    }
+                    run += v[q];
+                }
+                __syncthreads();
+                if (threadIdx.x == kBThreads - 1) s_carry = run;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) G.off[nbox] = G.n;
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 3: scatter into the new cell-sorted order
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
+            if (v < G.n) {
+                const int gv = G.node_off + v;
+                const int2 ks = a.keyslot[gv];
+                const int pos = G.off[ks.x] + ks.y;
+                const int i = a.vperm[cur][gv];
+                if ((unsigned)pos >= (unsigned)G.n || i < G.node_off || i >= G.node_off + G.n) {
+                    atomicOr(&st->flags, FLAG_SORT_RANGE);
+                } else {
+                    a.vxy[cur ^ 1][G.node_off + pos] = a.vxy[cur][gv];
+                    a.vperm[cur ^ 1][G.node_off + pos] = i;
+                }
+            }
+        }
+        grid.sync();
+
+        // ---- phase 4: spread, one thread per box
+        const int n_box_items = __ldg(a.pre_boxes + a.B);
+        for (int item = blockIdx.x; item < n_box_items; item += gridDim.x) {
+            const int g = owner(a.pre_boxes, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const GridDesc gd = st->grid;
+            const int b = (item - __ldg(a.pre_boxes + g)) * kBChunk + threadIdx.x;
+            if (b < gd.n_int * gd.n_int) {
+                const int by = b / gd.n_int;
+                const int bx = b - by * gd.n_int;
+                const float2* sxy = a.vxy[(int)(st->t_cur & 1) ^ 1] + G.node_off;
+                spread_box<K>(sxy, nullptr, max(G.off[b], 0), min(G.off[b + 1], G.n), bx, by, axis_geom(gd), G.gin,
+                              G.Gs);
+            }
+        }
+        grid.sync();
+
+        // ---- phase 5: forward row transforms (and kernel-sample rows on a rebuild)
+        const int n_row_items = __ldg(a.pre_rows + a.B);
+        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
+            const int g = owner(a.pre_rows, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            const int blk = item - __ldg(a.pre_rows + g);
+            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+            if (blk < data_blocks) {
+                GridSource gs;
+                gs.gin = G.gin;
+                gs.Gs = G.Gs;
+                rows_fwd_body<LOGP>(gs, st->grid.G, blk, G.T1, G.ystride, a.tw, sm);
+            } else if (st->spec_dirty) {
+                KernelSource ks;
+                ks.P = 1 << LOGP;
+                ks.bind(st, a.prm + g);
+                rows_fwd_body<LOGP>(ks, ks.P, blk - data_blocks, G.S1, 1 << LOGP, a.tw, sm);
+            }
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 6: column transforms, spectral product (spectrum rebuilt if needed)
+        const int n_col_items = __ldg(a.pre_cols + a.B);
+        for (int item = blockIdx.x; item < n_col_items; item += gridDim.x) {
+            const int g = owner(a.pre_cols, a.B, item);
+            const BGraph G = a.graphs[g];
+            const DevState* st = a.st + g;
+            cols_body<LOGP>(item - __ldg(a.pre_cols + g), G.T1, G.T2, G.ystride, G.specK, G.specHx, G.specHy, G.S1,
+                            a.tw, st->grid.G, st->spec_dirty, sm);
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 7: inverse row transforms into (A, O^x, O^y)
+        for (int item = blockIdx.x; item < n_row_items; item += gridDim.x) {
+            const int g = owner(a.pre_rows, a.B, item);
+            const BGraph G = a.graphs[g];
+            const int blk = item - __ldg(a.pre_rows + g);
+            const int data_blocks = (G.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+            if (blk < data_blocks) rows_inv_body<LOGP>(blk, G.T2, G.ystride, G.gout, G.Gs, a.tw, a.st[g].grid.G, sm);
+            __syncthreads();
+        }
+        grid.sync();
+
+        // ---- phase 8: back-projection + update in sorted order
+        for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
+            const int g = owner(a.pre_nodes, a.B, item);
+            const BGraph G = a.graphs[g];
+            DevState* st = a.st + g;
+            const int cur = (int)(st->t_cur & 1);
+            const int nxt = cur ^ 1;
+            const int chunk = item - __ldg(a.pre_nodes + g);
+            const int s = chunk * kBChunk + threadIdx.x;
+            float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
+            unsigned bad = 0;
+            if (s < G.n) {
+                const int gs = G.node_off + s;
+                const float2 p = a.vxy[nxt][gs];
+                const int i = a.vperm[nxt][gs];
+                if (i >= G.node_off && i < G.node_off + G.n) {
+                    const float2 fr = gather_frep<K>(p, axis_geom(st->grid), G.gout, G.Gs);
+                    sfx = fr.x;
+                    sfy = fr.y;
+                    if (a.eval) {
+                        a.frep[i] = fr;
+                    } else {
+                        const float2 fa = a.fatt[i];
+                        const float2 q = capped_step(p, make_float2(fr.x + fa.x, fr.y + fa.y), (float)st->step_cur);
+                        if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+                        a.xy[nxt][i] = q;
+                        a.vxy[nxt][gs] = q;
+                        mn = fminf(q.x, q.y);
+                        mx = fmaxf(q.x, q.y);
+                    }
+                }
+            }
+            if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
+            // per-chunk reduction; every chunk lies inside one graph
+            __shared__ float s_mn[kBThreads / 32], s_mx[kBThreads / 32], s_fx[kBThreads / 32], s_fy[kBThreads / 32];
+            mn = warp_min(mn);
+            mx = warp_max(mx);
+            sfx = warp_sumf(sfx);
+            sfy = warp_sumf(sfy);
+            const int w = threadIdx.x >> 5;
+            if (lane == 0) {
+                s_mn[w] = mn;
+                s_mx[w] = mx;
+                s_fx[w] = sfx;
+                s_fy[w] = sfy;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double fx = 0.0, fy = 0.0;
+                for (int q = 0; q < kBThreads / 32; ++q) {
+                    mn = fminf(mn, s_mn[q]);
+                    mx = fmaxf(mx, s_mx[q]);
+                    fx += s_fx[q];
+                    fy += s_fy[q];
+                }
+                if (!a.eval && mn <= mx) {
+                    atomicMin(&st->bbox[nxt][0], f2ord(mn));
+                    atomicMax(&st->bbox[nxt][1], f2ord(mx));
+                }
+                atomicAdd(&st->net_frep[0], fx);
+                atomicAdd(&st->net_frep[1], fy);
+                if (chunk == 0 && !a.eval && a.advance) st->iter = st->t_cur + 1;
+            }
+            __syncthreads();
+        }
+        grid.sync();
+    }
+}
+
+
+template <int LOGP, int K>
+cudaError_t batch_launch_t(const BatchArgs& a, int blocks, cudaStream_t s) {
+    const size_t smem = std::max(RegGeom<LOGP>::rows_smem, RegGeom<LOGP>::cols_smem);  // attribute set at creation
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kBThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch<LOGP, K>, a);
+}
+
+template <int LOGP, int K>
+cudaError_t batch_occupancy_t(int* blocks_per_sm) {
+    const size_t smem = std::max(RegGeom<LOGP>::rows_smem, RegGeom<LOGP>::cols_smem);
+    cudaError_t e = cudaFuncSetAttribute(k_batch<LOGP, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch<LOGP, K>, kBThreads, smem);
+}
+
+// Launch / occupancy of k_batch<logP, K> for logP in [7, 11] (RegGeom<LOGP>::T * CG equals
+// kBThreads for the FFT phases only there), defined in batch_k<K>.cu.
+template <int K>
+cudaError_t batch_launch_k(int logP, const BatchArgs& a, int blocks, cudaStream_t s);
+template <int K>
+cudaError_t batch_occupancy_k(int logP, int* blocks_per_sm);
+
+#define TFDP_BATCH_INSTANTIATE(K)                                                             \
+    template <>                                                                               \
+    cudaError_t batch_launch_k<K>(int logP, const BatchArgs& a, int blocks, cudaStream_t s) { \
+        switch (logP) {                                                                       \
+            case 7: return batch_launch_t<7, K>(a, blocks, s);                                \
+            case 8: return batch_launch_t<8, K>(a, blocks, s);                                \
+            case 9: return batch_launch_t<9, K>(a, blocks, s);                                \
+            case 10: return batch_launch_t<10, K>(a, blocks, s);                              \
+            case 11: return batch_launch_t<11, K>(a, blocks, s);                              \
+            default: return cudaErrorInvalidValue;                                            \
+        }                                                                                     \
+    }                                                                                         \
+    template <>                                                                               \
+    cudaError_t batch_occupancy_k<K>(int logP, int* blocks_per_sm) {                          \
+        switch (logP) {                                                                       \
+            case 7: return batch_occupancy_t<7, K>(blocks_per_sm);                            \
+            case 8: return batch_occupancy_t<8, K>(blocks_per_sm);                            \
+            case 9: return batch_occupancy_t<9, K>(blocks_per_sm);                            \
+            case 10: return batch_occupancy_t<10, K>(blocks_per_sm);                          \
+            case 11: return batch_occupancy_t<11, K>(blocks_per_sm);                          \
+            default: return cudaErrorInvalidValue;                                            \
+        }                                                                                     \
+    }
+
+}  // namespace bk
+}  // namespace tfdp
