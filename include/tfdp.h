@@ -113,7 +113,7 @@ typedef struct {
 
 /* Stages of one iteration, in launch order, for tfdp_get_stage_times. */
 enum {
-    TFDP_STAGE_SORT = 0,          /* FFT path: grid policy, box of each node, counting sort (6 kernels) */
+    TFDP_STAGE_SORT = 0,          /* FFT path: grid policy, box of each node, counting sort (4 kernels) */
     TFDP_STAGE_SPREAD = 1,        /* FFT path: Lagrange projection onto the grid */
     TFDP_STAGE_SPECTRUM = 2,      /* FFT path: kernel spectrum (returns at once when cached) */
     TFDP_STAGE_ROWS_FWD = 3,      /* FFT path: forward transform along x */

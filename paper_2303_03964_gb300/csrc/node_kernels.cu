@@ -1,14 +1,18 @@
 // node_kernels.cu -- per-node stages of one t-FDP iteration (arXiv 2303.03964).
 //
 //   k_bbox           layout square extremes (Sec. 3.4: [x_min, x_max]^2 over both axes)
+//   k_order_reset /  visit order after a position upload: caller order, or the last
+//   k_order_refresh  sorted order with the new positions
 //   k_grid           grid policy of the iteration (Sec. 3.4 "Choices of k"), one thread
-//   k_bin            box of every node (Sec. 3.4: "projecting each data point into the
-//                    corresponding grid square"), counting-sort histogram
-//   k_scan_*         exclusive scan of the box counts
-//   k_scatter        cell-sorted copy of the positions
-//   k_spread         Lagrange projection onto the k x k nodes of each box (Sec. 3.4,
-//                    step 1): rho, m^x, m^y; one thread owns one box, so no atomics
-//   k_attract        attraction over the CSR (Eq. newforce), caller order, on a side stream
+//   k_bin            box of every node (Sec. 3.4: each point is assigned to the grid
+//                    square that contains it) and its slot: counting-sort histogram
+//   k_scan_lookback  single-pass exclusive scan of the box counts
+//   k_scatter        cell-sorted copy of the positions and the permutation
+//   k_spread /       Lagrange projection onto the k x k nodes of each box (Sec. 3.4,
+//   k_spread_group   step 1): rho, m^x, m^y; one thread (or one lane group) owns a box,
+//                    so no atomics
+//   k_attract        attraction over the CSR (Eq. newforce), caller order, on a side
+//                    stream; a warp per node of degree > kHeavyDegree
 //   k_gather_update  back-projection (step 3) + capped step (update), cell-sorted order
 //   k_exact          tiled all-pairs repulsion (Eq. repfK), FP32
 //   k_edge_update    attraction + capped step for the exact path
