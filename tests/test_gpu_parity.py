@@ -430,3 +430,29 @@ def test_run_equals_upload_iterate_download(tfdp):
                 b = g.get_positions()
             outs.append((a, b))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("rep", ["fft", "exact"])
+def test_attraction_of_hubs(tfdp, rep):
+    """Degrees around the warp-per-node threshold (32, 33) and a star centre of degree
+    100,000: the attraction equals the oracle's on every node (thread-summed and
+    warp-summed nodes alike)."""
+    rng = np.random.default_rng(27)
+    n = 100_001
+    star = np.stack([np.zeros(n - 1, np.int64), np.arange(1, n)], 1)
+    # node 1 gets 31 more neighbours (degree 32), node 2 gets 32 more (degree 33)
+    extra = [(1, j) for j in range(3, 34)] + [(2, j) for j in range(40, 72)]
+    e = np.concatenate([star, np.array(extra, np.int64)]).astype(np.int32)
+    xy = rng.uniform(-150, 150, size=(n, 2)).astype(np.float32)
+    p = _params(tfdp, grid_max=255, rep_mode=tfdp.REP_EXACT if rep == "exact" else tfdp.REP_FFT)
+    if rep == "exact":
+        n_use = 20_001  # keep the O(n^2) repulsion small: a star of 20,000 leaves
+        e = e[(e[:, 0] < n_use) & (e[:, 1] < n_use)]
+        xy = xy[:n_use]
+        n = n_use
+    with tfdp.Graph(n, e, xy, p) as g:
+        _, fa = g.eval_forces()
+    ref = oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)
+    assert record("attraction_hubs_%s" % rep, rel_l2(fa, ref)) <= FORCE_TOL
+    for i in (0, 1, 2):  # the centre and the two threshold nodes, node by node
+        assert np.linalg.norm(fa[i] - ref[i]) <= FORCE_TOL * max(np.linalg.norm(ref[i]), 1e-30)
