@@ -134,19 +134,35 @@ __global__ void __launch_bounds__(kNodeThreads) k_bin(NodeLaunch a) {
     const float lo = st->grid.lo_f, h = st->grid.h_f;
     const int n_int = st->grid.n_int;
     const int lane = threadIdx.x & 31;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-        const float2 p = vxy[v];
+    // two visit slots per thread per round (base and base + blockDim): both position
+    // loads are in flight together; each round's lanes still cover consecutive slots
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+        const int v1 = base + (int)blockDim.x;
+        const bool has1 = v1 < a.n;
+        const float2 p0 = vxy[base];
+        const float2 p1 = has1 ? vxy[v1] : p0;
         float tq;
-        const int bx = box_of(p.x, lo, h, n_int, &tq);
-        const int by = box_of(p.y, lo, h, n_int, &tq);
-        const int key = by * n_int + bx;
+        const int key0 = box_of(p0.y, lo, h, n_int, &tq) * n_int + box_of(p0.x, lo, h, n_int, &tq);
+        const int key1 = box_of(p1.y, lo, h, n_int, &tq) * n_int + box_of(p1.x, lo, h, n_int, &tq);
         const unsigned active = __activemask();
-        const unsigned same = __match_any_sync(active, key);
-        const int leader = __ffs(same) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(a.cnt + key, __popc(same));
-        base = __shfl_sync(same, base, leader);
-        a.keyslot[v] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
+        {
+            const unsigned same = __match_any_sync(active, key0);
+            const int leader = __ffs(same) - 1;
+            int b = 0;
+            if (lane == leader) b = atomicAdd(a.cnt + key0, __popc(same));
+            b = __shfl_sync(same, b, leader);
+            a.keyslot[base] = make_int2(key0, b + __popc(same & ((1u << lane) - 1u)));
+        }
+        const unsigned act1 = __ballot_sync(active, has1);
+        if (has1) {
+            const unsigned same = __match_any_sync(act1, key1);
+            const int leader = __ffs(same) - 1;
+            int b = 0;
+            if (lane == leader) b = atomicAdd(a.cnt + key1, __popc(same));
+            b = __shfl_sync(same, b, leader);
+            a.keyslot[v1] = make_int2(key1, b + __popc(same & ((1u << lane) - 1u)));
+        }
     }
 }
 
@@ -309,21 +325,35 @@ __global__ void __launch_bounds__(kNodeThreads) k_scatter(NodeLaunch a) {
     const float2* __restrict__ vxy = a.vxy[cur];
     int* __restrict__ nperm = a.vperm[cur ^ 1];
     float2* __restrict__ nxy = a.vxy[cur ^ 1];
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-        const int2 ks = a.keyslot[v];
-        const int pos = a.off[ks.x] + ks.y;
-        if ((unsigned)pos >= (unsigned)a.n) {
-            atomicOr(&a.st->flags, FLAG_SORT_RANGE);
-            continue;
+    // two visit slots per thread per round so that the dependent loads (slot -> box
+    // offset) of both are in flight together
+    const int stride = 2 * gridDim.x * blockDim.x;
+    for (int base = 2 * blockIdx.x * blockDim.x + threadIdx.x; base < a.n; base += stride) {
+        const int vv[2] = {base, base + (int)blockDim.x};
+        int2 ks[2];
+        int ii[2];
+        float2 pp[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int v = vv[u] < a.n ? vv[u] : base;
+            ks[u] = a.keyslot[v];
+            ii[u] = vperm[v];
+            pp[u] = vxy[v];
         }
-        const int i = vperm[v];
-        if ((unsigned)i >= (unsigned)a.n) {
-            atomicOr(&a.st->flags, FLAG_SORT_RANGE);
-            continue;
+        int pos[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) pos[u] = a.off[ks[u].x] + ks[u].y;
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (vv[u] >= a.n) continue;
+            if ((unsigned)pos[u] >= (unsigned)a.n || (unsigned)ii[u] >= (unsigned)a.n) {
+                atomicOr(&a.st->flags, FLAG_SORT_RANGE);
+                continue;
+            }
+            nxy[pos[u]] = pp[u];
+            nperm[pos[u]] = ii[u];
+            if (a.vwr) a.vwr[pos[u]] = a.wrep[ii[u]];
         }
-        nxy[pos] = vxy[v];
-        nperm[pos] = i;
-        if (a.vwr) a.vwr[pos] = a.wrep[i];
     }
 }
 
@@ -667,10 +697,10 @@ cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s) {
 cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
     if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
-    const int nb = blocks_for(a.n, kNodeThreads);
-    cudaError_t e = launch_pdl(k_bin, nb, kNodeThreads, 0, s, a);
+    const int nb2 = blocks_for(a.n, 2 * kNodeThreads);  // two visit slots per thread
+    cudaError_t e = launch_pdl(k_bin, nb2, kNodeThreads, 0, s, a);
     if (e == cudaSuccess) e = launch_pdl(k_scan_lookback, scan_blocks, kScanThreads, 0, s, a, scan_blocks, a.scan_status);
-    if (e == cudaSuccess) e = launch_pdl(k_scatter, nb, kNodeThreads, 0, s, a);
+    if (e == cudaSuccess) e = launch_pdl(k_scatter, nb2, kNodeThreads, 0, s, a);
     return e;
 }
 
