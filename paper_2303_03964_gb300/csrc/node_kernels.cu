@@ -29,7 +29,8 @@
 
 namespace tfdp {
 
-constexpr int kScanThreads = 1024;
+constexpr int kScanThreads = 256;
+constexpr int kScanMaxTiles = 1024;  // tile status words the graph allocates
 constexpr int kScanItems = 8;
 constexpr int kScanChunk = kScanThreads * kScanItems;
 static_assert(kScanItems == 8, "k_scan_lookback moves its items as two int4");
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
     if (lane == 31) s_w[w] = incl;
     __syncthreads();
     if (w == 0) {
-        const int x = s_w[lane];
+        const int x = lane < kScanThreads / 32 ? s_w[lane] : 0;
         int xi = x;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -696,7 +697,7 @@ cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s) {
 
 cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
     const int scan_blocks = blocks_for(a.nbox_max, kScanChunk);
-    if (scan_blocks > kScanThreads) return cudaErrorInvalidValue;
+    if (scan_blocks > kScanMaxTiles) return cudaErrorInvalidValue;
     const int nb2 = blocks_for(a.n, 2 * kNodeThreads);  // two visit slots per thread
     cudaError_t e = launch_pdl(k_bin, nb2, kNodeThreads, 0, s, a);
     if (e == cudaSuccess) e = launch_pdl(k_scan_lookback, scan_blocks, kScanThreads, 0, s, a, scan_blocks, a.scan_status);
