@@ -349,6 +349,37 @@ def serving_measurement(jobs=200, rate=20.0, updates=5, init_iters=300, upd_iter
             "chunk_iters": chunk}
 
 
+def workload_measurement(name, stream, flush, steps, warmup):
+    """Device-resident throughput of another configuration's workload (same timing as the
+    main line: L2 flushed before each step, CUDA events around each step)."""
+    import torch
+    from paper_2303_03964_gb300 import tfdp
+    spec = WORKLOADS[name]
+    e, xy = make_workload(name)
+    n = xy.shape[0]
+    rep_mode = tfdp.REP_EXACT if spec["rep"] == "exact" else tfdp.REP_FFT
+    params = tfdp.params_default(rep_mode=rep_mode, k_interp=spec["k"], grid_max=spec["grid_max"],
+                                 total_iters=spec["total_iters"])
+    with tfdp.Graph(n, e, xy, params, stream=stream.cuda_stream) as g:
+        def step():
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.iterate(1)
+            e1.record(stream)
+            stream.synchronize()
+            return e0.elapsed_time(e1)
+        for _ in range(warmup):
+            step()
+        ms = [step() for _ in range(steps)]
+        st = g.stats()
+    return {"desc": spec["desc"], "rep": spec["rep"], "n": int(n), "m": int(e.shape[0]),
+            "value": n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
+            "grid_G": st["grid_G"], "fft_P": st["fft_P"], "device_flags": st["device_flags"]}
+
+
 def dynamic_k_measurement(e, xy, spec, stream, sampler=None):
     """One whole layout (total_iters iterations) of the same graph with the dynamic k
     schedule of Sec. 3.4 (k = 1 for 90 % of the iterations, then 2, then 3) against the
@@ -641,6 +672,10 @@ def run_ours(args):
     serving = None
     if not args.no_serving and args.workload == "lattice_1m":
         serving = serving_measurement(sampler=sampler)
+    others = None
+    if not args.no_workloads and args.workload == "lattice_1m":
+        others = {w: workload_measurement(w, stream, flush, min(args.steps, 20), args.warmup)
+                  for w in ("er_2000_exact", "sbm_100k", "ba_2m")}
     quality = None
     if not args.no_quality and args.workload == "lattice_1m":
         quality = quality_measurement()
@@ -664,6 +699,7 @@ def run_ours(args):
         "batched": batched,
         "serving": serving,
         "dynamic_k": dynamic_k,
+        "other_workloads": others,
         "quality": quality,
         "stages_ms": mean_stage,
         "stages_note": "5 steps after the timed region with every stage bracketed by events "
@@ -693,6 +729,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the SBM 100k / BA 2M / ER 2000 (exact) lines of the default run")
     ap.add_argument("--no-quality", action="store_true",
                     help="skip the exact-vs-ibFFT layout-quality comparison")
     ap.add_argument("--no-dynamic-k", action="store_true",
