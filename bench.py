@@ -50,6 +50,7 @@ WORKLOADS = {
 # unchanged (sha256 over STAGE_SOURCES). Captured with
 #   ncu --set full --clock-control none -k regex:k_cols_r -s 2 -c 1 -o prof_k_cols_r
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-batch --no-serving
+#       --no-dynamic-k --no-quality --no-workloads
 NCU_TRAFFIC = {
     ("lattice_1m", "cols"): {"bytes": 50457088 + 1247744, "sha": "2dc150c62eff26e8"},
 }
