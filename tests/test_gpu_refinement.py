@@ -25,6 +25,17 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a, np.float64) - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def record(name, value):
+    """Append a measured parity error to $TFDP_PARITY_LOG (JSON lines), if set."""
+    import json
+    import os
+    path = os.environ.get("TFDP_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": name, "value": value}) + "\n")
+    return value
+
+
 def _graph(n, seed, span):
     rng = np.random.default_rng(seed)
     e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
@@ -44,8 +55,8 @@ def test_exact_path_weighted_forces(tfdp):
         g.set_node_weights(wr, wa)
         fr, fa = g.eval_forces()
     x64 = xy.astype(np.float64)
-    assert rel_l2(fr, oracle.rep_exact(x64, 2.0, w=wr)) <= FORCE_TOL
-    assert rel_l2(fa, oracle.attraction(e, x64, 0.1, 8.0, w=wa)) <= FORCE_TOL
+    assert record("weights_exact_frep", rel_l2(fr, oracle.rep_exact(x64, 2.0, w=wr))) <= FORCE_TOL
+    assert record("weights_exact_fatt", rel_l2(fa, oracle.attraction(e, x64, 0.1, 8.0, w=wa))) <= FORCE_TOL
 
 
 def test_fft_path_weighted_forces(tfdp):
@@ -57,8 +68,9 @@ def test_fft_path_weighted_forces(tfdp):
         st = g.stats()
     grid = oracle.grid_policy(xy, 3, 50, 255, oracle.GRID_SNAP_H)
     ref = oracle.rep_fft(xy.astype(np.float64), 2.0, 3, grid=grid, P=st["fft_P"], xy_f32=xy, w=wr)
-    assert rel_l2(fr, ref) <= FORCE_TOL
-    assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0, w=wa)) <= FORCE_TOL
+    assert record("weights_fft_frep", rel_l2(fr, ref)) <= FORCE_TOL
+    assert record("weights_fft_fatt",
+                  rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0, w=wa))) <= FORCE_TOL
 
 
 def _fisheye(n, seed, span):
@@ -86,7 +98,7 @@ def test_fisheye_layout_exact_path(tfdp):
         out = g.get_positions()
         assert g.stats()["device_flags"] == 0
     ref = oracle.iterate(xy.astype(np.float64), e, 30, mode="exact", T=100, wrep=wr, watt=wa)
-    assert rel_l2(out, ref) <= POS_TOL
+    assert record("fisheye_exact_30it_pos", rel_l2(out, ref)) <= POS_TOL
 
 
 def test_fisheye_layout_fft_path(tfdp):
@@ -103,7 +115,7 @@ def test_fisheye_layout_fft_path(tfdp):
         assert g.stats()["device_flags"] == 0
     ref = oracle.iterate(xy.astype(np.float64), e, 3, mode="fft", k=3, grid_max=255,
                          policy=oracle.GRID_SNAP_H, P=512, T=300, wrep=wr, watt=wa)
-    assert rel_l2(out, ref) <= POS_TOL
+    assert record("fisheye_fft_3it_pos", rel_l2(out, ref)) <= POS_TOL
 
 
 @pytest.mark.parametrize("rep", ["exact", "fft"])
