@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<
 }
 
 template <int LOGP>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 4 : 1)
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 3 : 1)
     k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
                  const float2* __restrict__ tw, const DevState* __restrict__ st) {
     extern __shared__ float2 sm[];

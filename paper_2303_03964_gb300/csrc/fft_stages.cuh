@@ -240,21 +240,37 @@ __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict_
     constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
     const int ybase = blk * (2 * RG);
     if (ybase >= G) return;
-    // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum
-    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
-        const int c = idx / NH;
-        const int kx = split_freq<LOGP>(idx - c * NH);
-        const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
-        const int pk = swz(pos_of_freq<LOGP>(kx));
-        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+    // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum.
+    // NB items per thread and round: all their loads are in flight before the first store
+    constexpr int NB = (RG >= 4) ? 1 : 4 / RG;
+    for (int i0 = threadIdx.x; i0 < 3 * NH; i0 += NB * blockDim.x) {
+        float4 X[NB][RG];
 #pragma unroll
-        for (int q = 0; q < RG; ++q) {
-            const int y = ybase + 2 * q;
-            float4 X = (y < G) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (y + 1 >= G) { X.z = 0.f; X.w = 0.f; }  // row past G: never written
-            float2* seq = sm + ((size_t)q * 3 + c) * P;
-            seq[pk] = make_float2(X.x - X.w, X.y + X.z);
-            if (kx != 0 && kx != P / 2) seq[pn] = make_float2(X.x + X.w, X.z - X.y);
+        for (int b = 0; b < NB; ++b) {
+            const int idx = i0 + b * blockDim.x;
+            const int c = idx / NH;
+            const int kx = split_freq<LOGP>(idx - c * NH);
+            const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
+#pragma unroll
+            for (int q = 0; q < RG; ++q)
+                X[b][q] = (idx < 3 * NH && ybase + 2 * q < G) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int idx = i0 + b * blockDim.x;
+            if (idx >= 3 * NH) break;
+            const int c = idx / NH;
+            const int kx = split_freq<LOGP>(idx - c * NH);
+            const int pk = swz(pos_of_freq<LOGP>(kx));
+            const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+#pragma unroll
+            for (int q = 0; q < RG; ++q) {
+                float4 x = X[b][q];
+                if (ybase + 2 * q + 1 >= G) { x.z = 0.f; x.w = 0.f; }  // row past G: never written
+                float2* seq = sm + ((size_t)q * 3 + c) * P;
+                seq[pk] = make_float2(x.x - x.w, x.y + x.z);
+                if (kx != 0 && kx != P / 2) seq[pn] = make_float2(x.x + x.w, x.z - x.y);
+            }
         }
     }
     __syncthreads();
