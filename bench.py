@@ -43,6 +43,9 @@ WORKLOADS = {
                  "rep": "fft", "k": 3, "grid_max": 255, "total_iters": 500},
     "er_2000_exact": {"desc": "ER n=2000, m=8000, U[-50,50]^2, exact repulsion",
                       "rep": "exact", "k": 3, "grid_max": 255, "total_iters": 100},
+    # the exact all-pairs kernel at a size that fills the GPU (its FMA roofline)
+    "er_64k_exact": {"desc": "ER n=65,536, m=262,144, U[-128,128]^2, exact repulsion",
+                     "rep": "exact", "k": 3, "grid_max": 255, "total_iters": 100},
 }
 
 # DRAM bytes of the dominant kernel from one ncu capture, per launch, keyed by
@@ -79,6 +82,10 @@ def make_workload(name):
         e, xy = synth.sbm_100k()
     elif name == "er_2000_exact":
         e, xy = synth.er_2000()
+    elif name == "er_64k_exact":
+        rng = synth.rng_for(6)
+        e = synth.erdos_renyi(65536, 4 * 65536, rng)
+        xy = synth.uniform_positions(65536, 128.0, rng)
     else:
         raise KeyError(name)
     return e, xy
@@ -121,6 +128,14 @@ def source_sha(stage):
         with open(os.path.join(ROOT, "paper_2303_03964_gb300", "csrc", src), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def measured_peaks_raw():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
 
 
 def measured_peaks():
@@ -379,6 +394,42 @@ def workload_measurement(name, stream, flush, steps, warmup):
     return {"desc": spec["desc"], "rep": spec["rep"], "n": int(n), "m": int(e.shape[0]),
             "value": n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
             "grid_G": st["grid_G"], "fft_P": st["fft_P"], "device_flags": st["device_flags"]}
+
+
+def exact_kernel_measurement(stream, flush, steps, warmup, name="er_64k_exact"):
+    """The tiled exact all-pairs kernel (k_exact) at a size where it fills the GPU, against
+    the FP32 FMA peak. About 11 FP32 flops per pair at gamma = 2 (two differences, 1 + d^2
+    as two FMAs, r^2 and two FMA accumulations) plus one reciprocal on the quarter-rate
+    MUFU unit (16 per SM and clock), which caps it at 16 pairs per SM and clock, i.e.
+    11/16 of the all-FMA peak."""
+    import torch
+    from paper_2303_03964_gb300 import tfdp
+    e, xy = make_workload(name)
+    n = xy.shape[0]
+    params = tfdp.params_default(rep_mode=tfdp.REP_EXACT, total_iters=WORKLOADS[name]["total_iters"])
+    with tfdp.Graph(n, e, xy, params, stream=stream.cuda_stream) as g:
+        g.set_stage_timing_mask(["exact"])
+        times = []
+        for it in range(warmup + steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            g.iterate(1)
+            g.synchronize()
+            if it >= warmup:
+                times.append(g.stage_times()["exact"])
+        flags = g.stats()["device_flags"]
+    ms = statistics.fmean(times)
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    peaks = measured_peaks_raw()
+    clock_ghz = (peaks.get("sm_max_mhz") or 2070.0) / 1e3
+    fma_peak = sms * 128 * 2 * clock_ghz / 1e3  # TFLOP/s
+    ach = 11.0 * n * n / (ms * 1e-3) / 1e12
+    return {"kernel": "k_exact", "n": n, "pairs": n * n, "kernel_ms": ms, "bound": "alu",
+            "achieved": ach, "peak": fma_peak, "unit": "TFLOP/s", "frac": ach / fma_peak,
+            "pairs_per_s": n * n / (ms * 1e-3), "mix_ceiling_frac": 11.0 / 16.0,
+            "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 flop (FMA) x %.2f GHz" % (sms, clock_ghz),
+            "workload": name + ": " + WORKLOADS[name]["desc"] + ", gamma = 2, one launch per iteration",
+            "device_flags": flags}
 
 
 def dynamic_k_measurement(e, xy, spec, stream, sampler=None):
@@ -677,6 +728,9 @@ def run_ours(args):
     if not args.no_workloads and args.workload == "lattice_1m":
         others = {w: workload_measurement(w, stream, flush, min(args.steps, 20), args.warmup)
                   for w in ("er_2000_exact", "sbm_100k", "ba_2m")}
+    exact_kernel = None
+    if not args.no_workloads and args.workload == "lattice_1m":
+        exact_kernel = exact_kernel_measurement(stream, flush, min(args.steps, 10), args.warmup)
     quality = None
     if not args.no_quality and args.workload == "lattice_1m":
         quality = quality_measurement()
@@ -706,6 +760,7 @@ def run_ours(args):
         "serving": serving,
         "dynamic_k": dynamic_k,
         "other_workloads": others,
+        "exact_kernel": exact_kernel,
         "quality": quality,
         "stages_ms": mean_stage,
         "stages_note": "5 steps after the timed region with every stage bracketed by events "
@@ -736,7 +791,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-graph batched measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the SBM 100k / BA 2M / ER 2000 (exact) lines of the default run")
+                    help="skip the SBM 100k / BA 2M / ER 2000 (exact) lines and the exact-kernel "
+                         "roofline (n = 65536) of the default run")
     ap.add_argument("--no-quality", action="store_true",
                     help="skip the exact-vs-ibFFT layout-quality comparison")
     ap.add_argument("--no-dynamic-k", action="store_true",

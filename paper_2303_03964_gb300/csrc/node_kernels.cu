@@ -539,9 +539,47 @@ __device__ __forceinline__ float kernel_of(float u, float gamma) {
     return k;
 }
 
+// Paired FP32 operations of sm_100-family GPUs on (x, y) pairs held in a 64-bit register:
+// each lane rounds exactly like the scalar operation, so a pair op gives the same bits as
+// two scalar ones while taking one issue slot.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// One source (qx, qy) with weight wj on target pi2 = (x_i, y_i): (dx, dy) = x_i - x_j,
+// K = (1 + d^2)^-gamma (times wj), (fx, fy) += K (dx, dy).
+template <int GI, bool W>
+__device__ __forceinline__ void exact_pair(unsigned long long pi2, float qx, float qy, float wj, float gamma,
+                                           unsigned long long& f2) {
+    const unsigned long long d = f2_sub(pi2, f2_pack(qx, qy));
+    float dx, dy;
+    f2_unpack(d, dx, dy);
+    float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
+    if (W) K *= wj;
+    f2 = f2_fma(f2_pack(K, K), d, f2);
+}
+
 // Tiled all-pairs repulsion: each CTA owns kNodeThreads targets and one chunk of the
 // sources (blockIdx.y), staging source tiles in shared memory. Partial sums per chunk
-// go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic).
+// go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic). A full
+// tile is read two sources per 16-byte shared load; (dx, dy) and the (fx, fy) sums use
+// the paired operations.
 template <int GI, bool W>
 __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advance) {
     pdl_wait();
@@ -561,14 +599,15 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
         }
     }
     const float gamma = (float)a.prm->gamma;
-    __shared__ float2 tile[kNodeThreads];
-    __shared__ float tile_w[W ? kNodeThreads : 1];  // source weights r_j (local refinement)
+    __shared__ __align__(16) float2 tile[kNodeThreads];
+    __shared__ __align__(8) float tile_w[W ? kNodeThreads : 2];  // source weights r_j (local refinement)
     const int i = blockIdx.x * kNodeThreads + threadIdx.x;
     const float2 pi = (i < a.n) ? xy[i] : make_float2(0.f, 0.f);
+    const unsigned long long pi2 = f2_pack(pi.x, pi.y);
     const int csize = (a.n + a.nchunks - 1) / a.nchunks;
     const int j0 = blockIdx.y * csize;
     const int j1 = min(a.n, j0 + csize);
-    float fx = 0.0f, fy = 0.0f;
+    unsigned long long f2 = f2_pack(0.0f, 0.0f);
     for (int s0 = j0; s0 < j1; s0 += kNodeThreads) {
         const int j = s0 + threadIdx.x;
         tile[threadIdx.x] = (j < j1) ? xy[j] : pi;
@@ -576,27 +615,25 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
         __syncthreads();
         const int cnt = min(kNodeThreads, j1 - s0);
         if (cnt == kNodeThreads) {
-#pragma unroll 8
-            for (int jj = 0; jj < kNodeThreads; ++jj) {
-                const float2 q = tile[jj];
-                const float dx = pi.x - q.x, dy = pi.y - q.y;
-                float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
-                if (W) K *= tile_w[jj];
-                fx = fmaf(K, dx, fx);
-                fy = fmaf(K, dy, fy);
+            const float4* t4 = reinterpret_cast<const float4*>(tile);
+            const float2* w2 = reinterpret_cast<const float2*>(tile_w);
+#pragma unroll 4
+            for (int jj = 0; jj < kNodeThreads / 2; ++jj) {
+                const float4 q = t4[jj];  // sources 2 jj and 2 jj + 1, in that order
+                const float2 wq = W ? w2[jj] : make_float2(1.0f, 1.0f);
+                exact_pair<GI, W>(pi2, q.x, q.y, wq.x, gamma, f2);
+                exact_pair<GI, W>(pi2, q.z, q.w, wq.y, gamma, f2);
             }
         } else {
             for (int jj = 0; jj < cnt; ++jj) {
                 const float2 q = tile[jj];
-                const float dx = pi.x - q.x, dy = pi.y - q.y;
-                float K = kernel_of<GI>(fmaf(dx, dx, fmaf(dy, dy, 1.0f)), gamma);
-                if (W) K *= tile_w[jj];
-                fx = fmaf(K, dx, fx);
-                fy = fmaf(K, dy, fy);
+                exact_pair<GI, W>(pi2, q.x, q.y, W ? tile_w[jj] : 1.0f, gamma, f2);
             }
         }
         __syncthreads();
     }
+    float fx, fy;
+    f2_unpack(f2, fx, fy);
     if (i < a.n) a.part[(size_t)blockIdx.y * a.n + i] = make_float2(fx, fy);
 }
 

@@ -202,6 +202,24 @@ struct tfdp_graph {
 
 namespace {
 
+// Source chunks of the exact path for nb target CTAs: at least about four CTAs per SM in
+// total (nb * chunks >= 4 * 152), and among the next few counts the one whose CTAs
+// divide most evenly over the 152 SMs (every CTA does the same work).
+int exact_chunks(int nb) {
+    const int c0 = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+    int best = c0;
+    double best_imb = 1e30;
+    for (int c = c0; c <= std::min(nb, c0 + 8); ++c) {
+        const double per_sm = (double)nb * c / 152.0;
+        const double imb = std::ceil(per_sm) / per_sm;
+        if (imb < best_imb - 1e-9) {
+            best_imb = imb;
+            best = c;
+        }
+    }
+    return best;
+}
+
 DevParams make_dev_params(const tfdp_params& p, int P, int logP) {
     DevParams d{};
     d.alpha = p.alpha;
@@ -630,9 +648,9 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
         return cuda_fail(e, "create stream");
     }
 
-    // exact-path chunking: about four CTAs per SM in total
+    // exact-path chunking
     const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
-    g->nchunks = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+    g->nchunks = exact_chunks(nb);
 
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     Arena A;
@@ -953,7 +971,7 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
     if (st != TFDP_OK) return st;
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
-    const int nchunks = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+    const int nchunks = exact_chunks(nb);
     size_t b = 0;
     b += sizeof(float2) * nn * (4 + (size_t)nchunks) + sizeof(int) * (nn + 1) + sizeof(int) * (size_t)(2 * m);
     b += sizeof(int) * (size_t)std::min<int64_t>((int64_t)nn, 2 * m / (kHeavyDegree + 1) + 1);  // hub list bound
