@@ -97,8 +97,8 @@ def stage_bytes(stage, n, m, G, P, nbox):
     NH = P // 2 + 1
     if stage == "sort":
         # bin: read xy, write (key, slot); scan: cnt -> off; scatter: read (key, slot),
-        # xy, write sorted xy + perm
-        return 8 * n + 8 * n + 2 * 4 * nbox + (8 * n + 8 * n) + (8 * n + 4 * n)
+        # xy and the old permutation, write sorted xy and the new permutation
+        return 8 * n + 8 * n + 2 * 4 * nbox + (8 * n + 8 * n + 4 * n) + (8 * n + 4 * n)
     if stage == "spread":
         return 8 * n + 4 * nbox + 3 * 4 * G * G
     if stage == "rows_fwd":
