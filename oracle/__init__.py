@@ -1,7 +1,8 @@
 """FP64 CPU oracle for one t-FDP iteration (arXiv 2303.03964).
 
-TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may import this package. The GPU library shares no code with it.
+TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()``, and the CPU-baseline
+leg and the reference arm of ``bench.py`` may import this package (``build()`` compiles
+it). The GPU library shares no code with it.
 
 This module only marshals numpy arrays into the C oracle (``tfdp_oracle.c``); every
 step of the arithmetic is there, each function citing the section or equation of the

@@ -1,9 +1,9 @@
 /*
  * tfdp_oracle.c -- plain, slow, FP64 CPU oracle for one t-FDP iteration.
  *
- * TEST INFRASTRUCTURE. Only the tests, the smoke check and the benchmark's
- * CPU-baseline leg load this library. The GPU library shares no code with it
- * and never links it.
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check, and the benchmark's
+ * CPU-baseline leg and reference arm load this library. The GPU library shares no
+ * code with it and never links it.
  *
  * It follows "Force-directed graph layouts revisited: a new force based on the
  * t-Distribution" (Zhong, Xue, Zhang, Zhang, Ban, Deussen, Wang; arXiv 2303.03964):
@@ -15,12 +15,18 @@
  *                         each of N_int x N_int boxes over the layout square, grid
  *                         interaction by FFT, back-projection, then Eq. (Fr1)/(Fr2)
  *                         with the three kernel sums of Eq. (kernelproduct)
- *   grid size             Sec. 3.4 "Choices of k": N_int = max(50, [L])
+ *   grid size             Sec. 3.4 "Choices of k": N_int = max(50, [L]). Policy
+ *                         GRID_PAPER takes h = L / N_int; GRID_SNAP_H rounds h up to
+ *                         2^e (16 + j) / 16 so that the spectrum can be cached. SNAP_H
+ *                         is a reading, not the paper's: parity unpinned against the
+ *                         paper (the tests pin its arithmetic, not its choice).
  *   dynamic k             Sec. 3.4 "Choices of k": k = 1 for the first 90% of the
  *                         iterations, k = 2 for the next 5%, k = 3 for the rest
  *                         (boundaries floor(0.9 T), floor(0.95 T): a reading)
  *   position update       Sec. 3.1 (move along the resultant force until convergence);
- *                         the step schedule is a reading, the paper gives none.
+ *                         the step schedule is a reading, the paper gives none: parity
+ *                         unpinned against the paper (pinned only by the closed-form
+ *                         equilibria the iteration must reach).
  *   local refinement      Sec. 5 "Local Refinement" (fisheye views): stronger attraction
  *                         between focal nodes and their neighbours, stronger repulsion
  *                         elsewhere. The paper gives no formula; the reading is per-node
