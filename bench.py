@@ -119,6 +119,27 @@ def stage_bytes(stage, n, m, G, P, nbox):
     return 0
 
 
+def iteration_model_bytes(n, m, G, P):
+    """Single-pass byte model of one FFT-path iteration: node bytes 28 n + 24 m (the
+    spread reads the positions; gather, attraction and update read positions, row
+    pointers, column ids and the neighbours' positions and write the positions) plus
+    grid bytes 2 * 3 * 4 G^2 + 2 * 3 * P (P/2+1) * 8 + 3 * P (P/2+1) * 4 (each transform
+    one read and one write, the three kernel spectra read once)."""
+    NH = P // 2 + 1
+    return 28 * n + 24 * m + 2 * 3 * 4 * G * G + 2 * 3 * P * NH * 8 + 3 * P * NH * 4
+
+
+def iteration_roofline(n, m, G, P, ms_per_step, peak_gbs):
+    """Whole-iteration rate against HBM under iteration_model_bytes (None without a grid)."""
+    if not G or not P or ms_per_step <= 0:
+        return None
+    b = iteration_model_bytes(n, m, G, P)
+    ach = b / (ms_per_step * 1e-3) / 1e9
+    return {"bytes_per_iteration": b, "achieved": ach, "peak": peak_gbs, "unit": "GB/s",
+            "frac": ach / peak_gbs,
+            "model": "28 n + 24 m node bytes + 24 G^2 + 60 P (P/2+1) grid bytes per iteration"}
+
+
 def source_sha(stage):
     srcs = STAGE_SOURCES.get(stage)
     if not srcs:
@@ -766,6 +787,8 @@ def run_ours(args):
         "stages_note": "5 steps after the timed region with every stage bracketed by events "
                        "(the timed steps bracket only the roofline kernel)",
         "roofline": roof,
+        "iteration_roofline": (iteration_roofline(n, m, G, P, total_ms / args.steps, peak)
+                               if spec["rep"] == "fft" else None),
         "cpu_baseline": cpu,
         "e2e": {"value": ws * n * args.steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * n, "d2h_bytes_per_step": 8 * n},

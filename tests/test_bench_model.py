@@ -48,3 +48,15 @@ def test_workload_generators_sizes():
     assert xy.shape == (65536, 2) and e.shape == (4 * 65536, 2)
     e, xy = bench.make_workload("er_2000_exact")
     assert xy.shape == (2000, 2) and e.shape == (8000, 2)
+
+
+def test_iteration_model_bytes_lattice():
+    # node bytes 28 n + 24 m and the single-pass grid model at G = 1023, P = 2048:
+    # 76.0 MB + 151.1 MB
+    node = 28 * N + 24 * M
+    grid = 2 * 3 * 4 * G * G + 2 * 3 * P * NH * 8 + 3 * P * NH * 4
+    assert bench.iteration_model_bytes(N, M, G, P) == node + grid == 227_020_696
+    r = bench.iteration_roofline(N, M, G, P, 0.2270206960, 6753.1)
+    assert r["achieved"] == pytest.approx(1000.0)
+    assert r["frac"] == pytest.approx(1000.0 / 6753.1)
+    assert bench.iteration_roofline(N, M, 0, 0, 1.0, 6753.1) is None
