@@ -399,6 +399,23 @@ tfdp_status refresh_bbox(tfdp_graph* g) {
     return TFDP_OK;
 }
 
+// An FFT-mode graph always has its FFT buffers before an FFT kernel runs. A failed
+// reallocation (tfdp_set_params asking for a larger grid when device memory is short)
+// leaves the graph in FFT mode without them; then retry the allocation, redo what a new
+// arena needs (visit order, device parameters), or return the allocation's error.
+tfdp_status fft_ready(tfdp_graph* g) {
+    if (g->params.rep_mode != TFDP_REP_FFT || g->fft_mem || g->n == 0) return TFDP_OK;
+    tfdp_status st = alloc_fft(g);
+    if (st != TFDP_OK) return st;
+    const int slot = (int)(g->host_iter & 1);
+    CK(launch_order_reset(g->node_launch(), slot, g->stream));
+    g->order_valid[slot] = true;
+    st = upload_params(g);
+    if (st != TFDP_OK) return st;
+    CK(cudaStreamSynchronize(g->stream));
+    return TFDP_OK;
+}
+
 // Enqueue one iteration (advance = 1) or one force evaluation (advance = 0, eval = 1).
 // Stages selected by the timing mask are bracketed by event records. The records sit on
 // a branch of their own (forked from the stage's stream at each border, joined at the
@@ -779,6 +796,8 @@ tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
         g->host_iter += iters;
         return tfdp_set_iteration(g, g->host_iter);
     }
+    tfdp_status ready = fft_ready(g);
+    if (ready != TFDP_OK) return ready;
     // segments of constant k (one segment unless the dynamic schedule switches k); the
     // device derives the same k from its iteration counter
     int left = iters;
@@ -836,7 +855,9 @@ tfdp_status tfdp_set_iteration(tfdp_graph* g, int64_t t) {
 tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_device) {
     if (!g) return TFDP_ERR_INVALID_ARG;
     if (g->n == 0) return TFDP_OK;
-    tfdp_status st = enqueue_step(g, g->stream, 0, 1, g->k_now());
+    tfdp_status st = fft_ready(g);
+    if (st != TFDP_OK) return st;
+    st = enqueue_step(g, g->stream, 0, 1, g->k_now());
     if (st != TFDP_OK) return st;
     g->last_was_eval = true;
     g->order_valid[(g->host_iter & 1) ^ 1] = true;  // its sort wrote the other visit order
