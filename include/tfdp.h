@@ -376,13 +376,17 @@ tfdp_status tfdp_server_destroy(tfdp_server* s);
  * Exact repulsion without any device allocation, for callers that cannot allocate:
  * code running under a framework whose caching allocator owns the device memory pool
  * and forbids side allocations, and latency-critical loops where cudaMalloc / cudaFree
- * could synchronise the device. The paper has no counterpart of this entry point; its
- * arithmetic is the exact sum of Sec. 3.4 Eq. (repfK):
+ * could synchronise the device. The paper has no counterpart of this entry point. It
+ * computes the exact all-pairs repulsion
  *     frep(i) = sum_{j != i} (x_i - x_j) / (1 + |x_i - x_j|^2)^gamma.
- *   xy      device pointer, n x 2 FP32 positions (caller-owned, read only)
+ *   xy      device pointer on the current device, n x 2 FP32 positions, 8-byte aligned
+ *           (caller-owned, read only)
  *   n       0 <= n <= TFDP_NOALLOC_MAX_N, else TFDP_ERR_PARAM_RANGE
  *   gamma   > 1, else TFDP_ERR_PARAM_RANGE
- *   frep    device pointer, n x 2 FP32 output (caller-owned)
+ *   frep    device pointer on the current device, n x 2 FP32 output, 8-byte aligned
+ *           (caller-owned)
+ *   A NULL, misaligned, host or other-device pointer gives TFDP_ERR_INVALID_ARG before
+ *   anything is launched.
  *   stream  cudaStream_t the two kernels are enqueued on (NULL = legacy default);
  *           the call returns once they are enqueued
  * Its only scratch is a fixed 2 MiB array of partial sums inside the library; every

@@ -12,6 +12,7 @@
 // repulsion of Eq. (repfK), as in the graph API's exact path.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/tfdp.h"
@@ -112,11 +113,24 @@ int na_gamma_int(double g) {
 extern "C" tfdp_status tfdp_exact_repulsion_noalloc(const float* xy, int64_t n, double gamma, float* frep,
                                                     void* stream) {
     if (n < 0 || (n > 0 && (!xy || !frep))) return TFDP_ERR_INVALID_ARG;
+    // the kernels read and write whole float2 pairs: both pointers must be 8-byte aligned
+    if ((((uintptr_t)xy) | ((uintptr_t)frep)) & 7u) return TFDP_ERR_INVALID_ARG;
     if (n > kNaMaxN) return TFDP_ERR_PARAM_RANGE;  // beyond the fixed scratch
     if (!(gamma > 1.0) || gamma > 1e6) return TFDP_ERR_PARAM_RANGE;
     if (n == 0) return TFDP_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) return TFDP_ERR_CUDA;
+    // both buffers must be device (or managed) memory that the current device owns;
+    // cudaPointerGetAttributes allocates nothing
+    for (const void* ptr : {(const void*)xy, (const void*)frep}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+            cudaGetLastError();
+            return TFDP_ERR_INVALID_ARG;
+        }
+        if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) return TFDP_ERR_INVALID_ARG;
+        if (at.type == cudaMemoryTypeDevice && at.device != dev) return TFDP_ERR_INVALID_ARG;
+    }
     // One-time set-up on this device, with the device current: the device address of
     // the scratch array.
     std::call_once(g_setup_once[dev], [dev]() {

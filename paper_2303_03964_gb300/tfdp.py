@@ -150,6 +150,16 @@ def _is_torch_cuda(x):
     return hasattr(x, "is_cuda") and hasattr(x, "data_ptr") and x.is_cuda
 
 
+def _check_device_f32(t, numel, what):
+    """A CUDA tensor passed as a device pointer: contiguous float32 with `numel` values."""
+    import torch
+
+    if t.dtype != torch.float32:
+        raise TypeError("%s must be float32" % what)
+    if not t.is_contiguous() or t.numel() != numel:
+        raise ValueError("%s must be contiguous with %d values" % (what, numel))
+
+
 def _host_f32(x, n):
     a = np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(n, 2))
     return a
@@ -210,7 +220,7 @@ class Graph:
     # ------------------------------------------------------------ positions
     def set_positions(self, xy):
         if _is_torch_cuda(xy):
-            assert xy.is_contiguous() and xy.numel() == 2 * self.n
+            _check_device_f32(xy, 2 * self.n, "xy")
             _check(lib.tfdp_set_positions(self._h, _p(xy.data_ptr()), 1), "tfdp_set_positions")
         else:
             a = _host_f32(xy, self.n)
@@ -226,7 +236,9 @@ class Graph:
             if w is None:
                 ptrs.append(None)
             elif dev:
-                assert _is_torch_cuda(w) and w.is_contiguous() and w.numel() == self.n
+                if not _is_torch_cuda(w):
+                    raise TypeError("weights must both be CUDA tensors or both host arrays")
+                _check_device_f32(w, self.n, "weight")
                 ptrs.append(_p(w.data_ptr()))
             else:
                 a = np.ascontiguousarray(np.asarray(w, dtype=np.float32).reshape(-1))
@@ -239,9 +251,13 @@ class Graph:
     def get_positions(self, out=None):
         """Positions as an (n, 2) float32 numpy array, or into `out` (numpy or CUDA tensor)."""
         if out is not None and _is_torch_cuda(out):
+            _check_device_f32(out, 2 * self.n, "out")
             _check(lib.tfdp_get_positions(self._h, _p(out.data_ptr()), 1), "tfdp_get_positions")
             return out
         a = out if out is not None else np.empty((self.n, 2), dtype=np.float32)
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous
+                and a.size == 2 * self.n):
+            raise ValueError("out must be a contiguous float32 numpy array of n x 2 values")
         _check(lib.tfdp_get_positions(self._h, a.ctypes.data_as(_p), 0), "tfdp_get_positions")
         return a
 
@@ -251,7 +267,9 @@ class Graph:
         iterations and download into `xy_out` (host, (n, 2) float32) in one call."""
         src = None if xy_in is None else _host_f32(xy_in, self.n)  # kept alive across the call
         pin = None if src is None else src.ctypes.data_as(_p)
-        assert xy_out.dtype == np.float32 and xy_out.flags.c_contiguous and xy_out.size == 2 * self.n
+        if not (isinstance(xy_out, np.ndarray) and xy_out.dtype == np.float32 and xy_out.flags.c_contiguous
+                and xy_out.size == 2 * self.n):
+            raise ValueError("xy_out must be a contiguous float32 numpy array of n x 2 values")
         _check(lib.tfdp_run(self._h, pin, int(iters), xy_out.ctypes.data_as(_p)), "tfdp_run")
         return xy_out
 
@@ -319,10 +337,20 @@ def exact_repulsion_noalloc(xy, frep, gamma=2.0, stream=0):
     of shape (n, 2), n <= NOALLOC_MAX_N. Asynchronous on ``stream``. All calls share one
     fixed scratch array in the library: calls that may overlap on the GPU race.
     """
+    import torch
+
     if not (_is_torch_cuda(xy) and _is_torch_cuda(frep)):
         raise TypeError("xy and frep must be CUDA tensors")
-    assert xy.is_contiguous() and frep.is_contiguous() and xy.numel() == frep.numel()
-    n = xy.numel() // 2
+    if xy.dtype != torch.float32 or frep.dtype != torch.float32:
+        raise TypeError("xy and frep must be float32")
+    if xy.dim() != 2 or xy.shape[1] != 2 or tuple(frep.shape) != tuple(xy.shape):
+        raise ValueError("xy and frep must both have shape (n, 2)")
+    if not (xy.is_contiguous() and frep.is_contiguous()):
+        raise ValueError("xy and frep must be contiguous")
+    cur = torch.cuda.current_device()
+    if xy.device.index != cur or frep.device.index != cur:
+        raise ValueError("xy and frep must be on the current CUDA device (%d)" % cur)
+    n = xy.shape[0]
     _check(lib.tfdp_exact_repulsion_noalloc(_p(xy.data_ptr()), n, float(gamma),
                                             _p(frep.data_ptr()), _p(stream or 0)),
            "tfdp_exact_repulsion_noalloc")

@@ -88,3 +88,19 @@ def test_bad_graph_rejected_before_any_device_work(edges):
 def test_status_strings():
     for code, name in tfdp.STATUS.items():
         assert tfdp.lib.tfdp_status_str(code).decode() == name
+
+
+@pytest.mark.parametrize("xy,frep", [(0x1001, 0x2000), (0x1000, 0x2004), (0x1002, 0x2006)])
+def test_noalloc_rejects_misaligned_pointers_before_any_launch(xy, frep):
+    # the kernels read and write float2 pairs: a pointer that is not 8-byte aligned is
+    # refused on the host, before any CUDA call (these addresses are never dereferenced)
+    st = tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(xy), 10, 2.0, tfdp._p(frep), None)
+    assert st == 1
+
+
+def test_noalloc_rejects_null_and_size_before_any_launch():
+    assert tfdp.lib.tfdp_exact_repulsion_noalloc(None, 10, 2.0, tfdp._p(0x2000), None) == 1
+    assert tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(0x1000), -1, 2.0, tfdp._p(0x2000), None) == 1
+    big = tfdp.NOALLOC_MAX_N + 1
+    assert tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(0x1000), big, 2.0, tfdp._p(0x2000), None) == 3
+    assert tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(0x1000), 10, 1.0, tfdp._p(0x2000), None) == 3

@@ -81,6 +81,29 @@ def test_exact_two_nodes_direction_and_magnitude():
         np.testing.assert_allclose(f[1], -f[0], rtol=1e-14)
 
 
+@pytest.mark.parametrize("weighted", [False, True])
+@pytest.mark.parametrize("gamma", [2.0, 3.3])
+def test_exact_rows_are_the_rows_of_the_full_sum(weighted, gamma):
+    """The row-sampled exact sum (used against the GPU at full size) must give, for every
+    listed target, the row of the full sum of Eq. (repfK): shuffled, repeated, first and
+    last rows, with and without local-refinement weights (reading R13)."""
+    rng = np.random.default_rng(41)
+    n = 301
+    xy = rng.uniform(-6.0, 6.0, size=(n, 2))
+    w = rng.uniform(0.25, 4.0, size=n) if weighted else None
+    full = oracle.rep_exact(xy, gamma, w=w)
+    rows = np.concatenate([rng.permutation(n)[:120], [0, n - 1, 7, 7, 7, 0]])
+    got = oracle.rep_exact(xy, gamma, rows=rows, w=w)
+    assert got.shape == (rows.shape[0], 2)
+    assert np.array_equal(got, full[rows])
+    # two nodes: the closed form of the t-force on the listed row alone
+    two = np.array([[0.3, -0.2], [1.1, 0.4]])
+    f1 = oracle.rep_exact(two, gamma, rows=[1])[0]
+    dvec = two[1] - two[0]
+    d = np.linalg.norm(dvec)
+    np.testing.assert_allclose(f1, oracle.tforce(d, gamma) * dvec / d, rtol=1e-14)
+
+
 @pytest.mark.parametrize("gamma", [2.0, 2.7, 4.0])
 def test_forces_are_minus_energy_gradient(gamma):
     """Central finite differences of an energy written independently of the forces."""

@@ -49,6 +49,46 @@ def test_noalloc_exact_repulsion_matches_graph_api_twice():
         assert _rel(got, oracle.rep_exact(xy.astype(np.float64), 2.0)) <= FORCE_TOL
 
 
+@pytest.mark.parametrize("gamma", [1.5, 2.0, 3.2, 4.0, 8.0])
+@pytest.mark.parametrize("n", [11, 777])
+def test_noalloc_every_gamma_branch_against_oracle(gamma, n):
+    # gamma 2, 4, 8 take the squaring branch; 1.5 and 3.2 the general exp2/log2 one.
+    # n = 11 leaves most of the 16 source chunks empty.
+    import torch
+    from paper_2303_03964_gb300 import tfdp
+
+    rng = np.random.default_rng(1000 + n)
+    xy = rng.uniform(-0.4 * np.sqrt(n), 0.4 * np.sqrt(n), size=(n, 2)).astype(np.float32)
+    xy_d = torch.from_numpy(xy).cuda()
+    out = torch.full_like(xy_d, float("nan"))
+    tfdp.exact_repulsion_noalloc(xy_d, out, gamma=gamma)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert _rel(got, oracle.rep_exact(xy.astype(np.float64), gamma)) <= FORCE_TOL
+
+
+def test_noalloc_rejects_tensors_the_kernels_cannot_read():
+    import torch
+    from paper_2303_03964_gb300 import tfdp
+
+    xy = torch.zeros((64, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(TypeError):
+        tfdp.exact_repulsion_noalloc(xy.double(), torch.empty_like(xy).double())
+    with pytest.raises(ValueError):
+        tfdp.exact_repulsion_noalloc(xy, torch.empty((32, 2), dtype=torch.float32, device="cuda"))
+    # an odd float offset is not 8-byte aligned: the library refuses it before launching
+    flat = torch.zeros(2 * 64 + 1, dtype=torch.float32, device="cuda")
+    st = tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(flat.data_ptr() + 4), 64, 2.0,
+                                               tfdp._p(xy.data_ptr()), None)
+    assert st == 1
+    # host memory is refused too
+    host = np.zeros((64, 2), np.float32)
+    st = tfdp.lib.tfdp_exact_repulsion_noalloc(host.ctypes.data_as(tfdp._p), 64, 2.0,
+                                               tfdp._p(xy.data_ptr()), None)
+    assert st == 1
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     import torch
     from paper_2303_03964_gb300 import tfdp
