@@ -172,6 +172,14 @@ tfdp_status tfdp_get_params(const tfdp_graph* g, tfdp_params* out);
 /* Overwrite all positions (n x 2 FP32, caller order). Asynchronous on the stream. */
 tfdp_status tfdp_set_positions(tfdp_graph* g, const float* xy, int on_device);
 
+/* Device-side checks. The synchronising calls tfdp_synchronize, tfdp_get_positions,
+ * tfdp_eval_forces and tfdp_run report the device flags raised since their last report:
+ * TFDP_ERR_TIMEOUT when a bounded device-side wait gave up, TFDP_ERR_DEVICE_CHECK for
+ * any other failed check (a position that became NaN or infinite, a box or sorted slot
+ * out of range). Outputs are written all the same; the flags are then cleared, the
+ * visit order of the next iteration restarts from the caller order, and
+ * tfdp_stats.device_flags keeps every flag seen. */
+
 /* Copy positions (n x 2 FP32, caller order) out. Synchronises the stream. */
 tfdp_status tfdp_get_positions(tfdp_graph* g, float* xy, int on_device);
 
@@ -401,6 +409,30 @@ tfdp_status tfdp_server_destroy(tfdp_server* s);
 #define TFDP_NOALLOC_MAX_N 16384
 tfdp_status tfdp_exact_repulsion_noalloc(const float* xy, int64_t n, double gamma, float* frep,
                                          void* stream);
+
+/*
+ * Test hooks for failure detection (the paper has no counterpart). They make a failure
+ * happen on the host, or as a bounded device-side wait that runs out; neither faults
+ * the GPU.
+ *   TFDP_INJECT_FFT_ALLOC   refuse the graph's next `value` FFT-buffer allocations as if
+ *                           the device had no memory left (host side: nothing reaches
+ *                           the device). The call that needed the buffers returns
+ *                           TFDP_ERR_OUT_OF_MEMORY; an FFT-mode graph left without them
+ *                           retries the allocation in its next tfdp_iterate or
+ *                           tfdp_eval_forces and launches nothing until it succeeds.
+ *   TFDP_INJECT_SCAN_STALL  value > 0: from the next iteration on, the first tile of the
+ *                           box-count scan (the counting sort of Sec. 3.4's projection)
+ *                           withholds its status word and every look-back wait gives up
+ *                           after `value` polls, so the waits of the later tiles run out;
+ *                           the kernel records this in the device flags and returns, and
+ *                           the next synchronising call (tfdp_synchronize,
+ *                           tfdp_get_positions, tfdp_eval_forces, tfdp_run) returns
+ *                           TFDP_ERR_TIMEOUT. value = 0 restores normal operation.
+ *                           Synchronises the stream.
+ * TFDP_ERR_INVALID_ARG for an unknown `what` or value < 0.
+ */
+enum { TFDP_INJECT_FFT_ALLOC = 1, TFDP_INJECT_SCAN_STALL = 2 };
+tfdp_status tfdp_debug_inject(tfdp_graph* g, int what, int value);
 
 /*
  * Test hook: copy an internal buffer of the last FFT-mode force evaluation to host

@@ -106,9 +106,35 @@ struct tfdp_batch {
     cudaGraphExec_t exec = nullptr;
     int exec_iters = -1;
     bool no_graph = false;
+    std::vector<unsigned> flags_word;  // device flags read back per graph
+    std::vector<unsigned> flags_seen;  // every flag reported so far per graph
 };
 
 namespace {
+
+// Wait for the batch's stream and report the device flags that graphs [g0, g1) raised
+// since the last report (TFDP_ERR_TIMEOUT for a wait that gave up, else
+// TFDP_ERR_DEVICE_CHECK); the flags are then cleared on the device and kept per graph
+// for tfdp_batch_get_stats.
+tfdp_status batch_sync_checked(tfdp_batch* b, int g0, int g1) {
+    const int cnt = g1 - g0;
+    if (cnt > 0) {
+        BK(cudaMemcpy2DAsync(b->flags_word.data() + g0, sizeof(unsigned), &b->d_st[g0].flags, sizeof(DevState),
+                             sizeof(unsigned), (size_t)cnt, cudaMemcpyDeviceToHost, b->stream));
+    }
+    BK(cudaStreamSynchronize(b->stream));
+    unsigned all = 0;
+    for (int q = g0; q < g1; ++q) {
+        const unsigned f = b->flags_word[(size_t)q];
+        if (!f) continue;
+        all |= f;
+        b->flags_seen[(size_t)q] |= f;
+        BK(cudaMemsetAsync(&b->d_st[q].flags, 0, sizeof(unsigned), b->stream));
+    }
+    if (!all) return TFDP_OK;
+    BK(cudaStreamSynchronize(b->stream));
+    return (all & FLAG_WAIT_TIMEOUT) ? TFDP_ERR_TIMEOUT : TFDP_ERR_DEVICE_CHECK;
+}
 
 cudaError_t batch_launch(const tfdp_batch* b, const BatchArgs& a, cudaStream_t s) {
     switch (b->k) {
@@ -189,6 +215,8 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
     b->B = num_graphs;
     b->stream = (cudaStream_t)stream;
     b->params.resize((size_t)num_graphs);
+    b->flags_word.assign((size_t)num_graphs, 0u);
+    b->flags_seen.assign((size_t)num_graphs, 0u);
     int G_need = 0;
     for (int g = 0; g < num_graphs; ++g) {
         tfdp_params p;
@@ -458,8 +486,7 @@ tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, fl
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (frep) BK(cudaMemcpyAsync(frep, a.frep + o, sizeof(float2) * ng, kind, b->stream));
     if (fatt) BK(cudaMemcpyAsync(fatt, a.fatt + o, sizeof(float2) * ng, kind, b->stream));
-    BK(cudaStreamSynchronize(b->stream));
-    return TFDP_OK;
+    return batch_sync_checked(b, graph, graph + 1);
 }
 
 tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, int on_device) {
@@ -467,8 +494,7 @@ tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, in
     const int slot = (int)(b->host_iter & 1);
     BK(cudaMemcpyAsync(xy, b->args.xy[slot] + b->node_off[(size_t)graph], sizeof(float2) * (size_t)b->n[(size_t)graph],
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->stream));
-    BK(cudaStreamSynchronize(b->stream));
-    return TFDP_OK;
+    return batch_sync_checked(b, graph, graph + 1);
 }
 
 tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) {
@@ -486,15 +512,14 @@ tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) 
     out->grid_G = s.grid.G;
     out->fft_P = b->P;
     out->spectrum_builds = s.spec_builds;
-    out->device_flags = (int32_t)s.flags;
+    out->device_flags = (int32_t)(s.flags | b->flags_seen[(size_t)graph]);
     out->kernels_per_iteration = 0;  // all iterations of a call share one launch
     return TFDP_OK;
 }
 
 tfdp_status tfdp_batch_synchronize(tfdp_batch* b) {
     if (!b) return TFDP_ERR_INVALID_ARG;
-    BK(cudaStreamSynchronize(b->stream));
-    return TFDP_OK;
+    return batch_sync_checked(b, 0, b->B);
 }
 
 tfdp_status tfdp_batch_destroy(tfdp_batch* b) {

@@ -66,6 +66,11 @@ struct DevParams {
     int gamma_int;   // gamma if it is a small integer (2..8), else 0
     int spread_shift; // fixed-point scale of the spread sums is 2^(27 - spread_shift)
     const double* step_table;  // s_t for t = 0 .. total_iters - 1 (host-computed, FP64)
+    // failure-detection test hook (0, 0 in normal operation): polls before a look-back
+    // wait of the box-count scan gives up (0 = the built-in limit), and whether the first
+    // scan tile withholds its status so that the waits of the later tiles run out
+    int scan_spin_limit;
+    int scan_stall;
 };
 
 // Grid of one iteration, Sec. 3.4: square [lo, lo + N_int h]^2, N_int x N_int boxes,

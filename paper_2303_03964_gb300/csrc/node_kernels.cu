@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
     if (threadIdx.x == 0) s_ticket = atomicAdd(&st->scan_ticket, 1ULL);
     __syncthreads();
     const unsigned long long tk = s_ticket;
+    const int spin_limit = a.prm->scan_spin_limit > 0 ? a.prm->scan_spin_limit : kLookbackSpinLimit;
+    const bool stall = a.prm->scan_stall != 0;
     const int tile = (int)(tk % (unsigned long long)ntiles);
     const unsigned long long epoch = (tk / (unsigned long long)ntiles) & 0x3FFFFFFFULL;
     const int n_int = st->grid.n_int;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
         volatile unsigned long long* vs = status;
         int prefix = 0;
         if (tile == 0) {
-            if (lane == 0) vs[0] = kStPrefix | tag | (unsigned)total;
+            if (lane == 0 && !stall) vs[0] = kStPrefix | tag | (unsigned)total;
         } else {
             if (lane == 0) {
                 vs[tile] = kStAggregate | tag | (unsigned)total;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_lookback(NodeLaunch a, in
                     ready = ((sw >> 32) & 0x3FFFFFFFULL) == epoch && (sw >> 62) != 0;
                 }
                 if (__all_sync(0xffffffffu, ready) == 0) {
-                    if (++spins > kLookbackSpinLimit) {
+                    if (++spins > spin_limit) {
                         if (lane == 0) atomicOr(&st->flags, FLAG_WAIT_TIMEOUT);
                         break;
                     }

@@ -2,11 +2,12 @@
 //
 // Jobs (a graph plus a queue of requests) are admitted by device-memory footprint
 // into at most `max_active` slots; each admitted job owns a tfdp_graph on its own CUDA
-// stream. A worker thread advances every admitted job with work by up to
-// `chunk_iters` iterations per tick, all jobs' work queued before any wait, so the
-// jobs' kernels overlap on the GPU; jobs that arrive while others run are admitted as
-// soon as a slot and memory are free (iteration-level scheduling, not a FIFO of whole
-// jobs). A request is either the initial layout of a job or an update: new t-force
+// stream. A worker thread keeps one chunk of up to `chunk_iters` iterations queued for
+// every admitted job with work: it polls the jobs' completion events and gives each job
+// its next chunk as soon as that job's previous chunk is done, so the jobs' kernels
+// overlap on the GPU and a small job never waits for a large one. Jobs that arrive
+// while others run are admitted as soon as a slot and memory are free (iteration-level
+// scheduling, not a FIFO of whole jobs). A request is either the initial layout of a job or an update: new t-force
 // parameters (Sec. 3.3) applied to the current layout with the step schedule restarted
 // over the update's iterations (warm start; the global refinement of Sec. 5). The
 // kernel spectrum is rebuilt only when gamma, k or the grid change. The computation of
@@ -14,6 +15,7 @@
 // result alone.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -52,7 +54,8 @@ struct Job {
     std::deque<Request> queue;
     bool admitted = false;
     bool release = false;
-    int32_t issued = 0;  // iterations queued in the current tick
+    int32_t issued = 0;  // iterations of the chunk in flight
+    bool in_flight = false;  // a chunk of this job is queued on the GPU
     int32_t error = 0;
 };
 
@@ -79,6 +82,7 @@ struct tfdp_server {
     int64_t node_iterations = 0;
     int32_t active = 0;
     int32_t peak_active = 0;
+    std::atomic<bool> kick{false};  // new work for an idle job: stop polling the GPU early
 
     void run();
     void load();
@@ -151,20 +155,54 @@ void tfdp_server::load() {
         j->edges.clear();
         j->edges.shrink_to_fit();
         j->admitted = true;
+        kick.store(true);
         cv_work.notify_all();
     }
 }
 
 void tfdp_server::run() {
     cudaSetDevice(device);
+    // jobs with a chunk queued on the GPU, and the request each chunk belongs to (the
+    // pointer is taken under the lock; other threads only append to a job's queue, which
+    // leaves its elements in place)
+    std::vector<std::pair<Job*, Request*>> inflight;
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
-        // queue one chunk of work for every admitted job that has a request
-        std::vector<Job*> busy;
+        // jobs ready for their next chunk: admitted, a request queued, nothing in flight
+        std::vector<std::pair<Job*, Request*>> ready;
+        kick.store(false);
         for (auto& kv : jobs) {
             Job* j = kv.second.get();
-            if (!j->admitted || j->queue.empty()) continue;
-            Request& r = j->queue.front();
+            if (j->admitted && !j->in_flight && !j->queue.empty()) ready.emplace_back(j, &j->queue.front());
+        }
+        // free the slots of released, drained jobs
+        for (auto it = jobs.begin(); it != jobs.end();) {
+            Job* j = it->second.get();
+            if (j->release && j->queue.empty() && !j->in_flight && (j->admitted || j->error)) {
+                if (j->g) tfdp_destroy_graph(j->g);
+                if (j->ev) cudaEventDestroy(j->ev);
+                if (j->stream) cudaStreamDestroy(j->stream);
+                if (j->admitted) {
+                    used -= j->footprint;
+                    --active;
+                    cv_load.notify_all();
+                }
+                it = jobs.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        if (ready.empty() && inflight.empty()) {
+            cv_work.wait_for(lk, std::chrono::milliseconds(20));
+            continue;
+        }
+        for (auto& jr : ready) jr.first->in_flight = true;
+        // queue the chunks without holding the lock: clients may submit and poll meanwhile,
+        // and a parameter change synchronises only the job's own stream
+        lk.unlock();
+        for (auto& jr : ready) {
+            Job* j = jr.first;
+            Request& r = *jr.second;
             if (!r.started) {
                 r.started = true;
                 r.t_start = now_s();
@@ -179,42 +217,46 @@ void tfdp_server::run() {
                 }
             }
             j->issued = r.remaining < chunk ? r.remaining : chunk;
-            if (j->issued > 0 && tfdp_iterate(j->g, j->issued) != TFDP_OK) {
-                j->error = TFDP_ERR_CUDA;
-                j->issued = 0;
-                r.remaining = 0;
-            }
-            cudaEventRecord(j->ev, j->stream);
-            busy.push_back(j);
-        }
-        if (busy.empty()) {
-            // release finished jobs, then sleep until something arrives
-            for (auto it = jobs.begin(); it != jobs.end();) {
-                Job* j = it->second.get();
-                if (j->release && j->queue.empty() && (j->admitted || j->error)) {
-                    if (j->g) tfdp_destroy_graph(j->g);
-                    if (j->ev) cudaEventDestroy(j->ev);
-                    if (j->stream) cudaStreamDestroy(j->stream);
-                    if (j->admitted) {
-                        used -= j->footprint;
-                        --active;
-                        cv_load.notify_all();
-                    }
-                    it = jobs.erase(it);
-                } else {
-                    ++it;
+            if (j->issued > 0) {
+                const tfdp_status st = tfdp_iterate(j->g, j->issued);
+                if (st != TFDP_OK) {
+                    j->error = st;
+                    j->issued = 0;
+                    r.remaining = 0;
                 }
             }
-            cv_work.wait_for(lk, std::chrono::milliseconds(20));
-            continue;
+            cudaEventRecord(j->ev, j->stream);
+            inflight.push_back(jr);
         }
-        // wait for the tick's work without holding the lock (clients may submit)
-        lk.unlock();
-        for (Job* j : busy) cudaEventSynchronize(j->ev);
+        // take whatever has finished, without waiting for the slowest job: each job gets
+        // its next chunk as soon as its own previous one is done
+        std::vector<std::pair<Job*, Request*>> finished;
+        for (;;) {
+            for (auto it = inflight.begin(); it != inflight.end();) {
+                if (cudaEventQuery(it->first->ev) == cudaErrorNotReady) {
+                    ++it;
+                    continue;
+                }
+                finished.push_back(*it);
+                it = inflight.erase(it);
+            }
+            if (!finished.empty() || inflight.empty() || kick.load()) break;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        // a request that ends with this chunk reports the job's device-side checks
+        for (auto& jr : finished) {
+            Job* j = jr.first;
+            if (jr.second->remaining - j->issued <= 0 && j->error == TFDP_OK) {
+                const tfdp_status st = tfdp_synchronize(j->g);
+                if (st != TFDP_OK) j->error = st;
+            }
+        }
         lk.lock();
         const double t = now_s();
-        for (Job* j : busy) {
-            Request& r = j->queue.front();
+        for (auto& jr : finished) {
+            Job* j = jr.first;
+            Request& r = *jr.second;
+            j->in_flight = false;
             r.remaining -= j->issued;
             node_iterations += (int64_t)j->issued * j->n;
             if (r.remaining <= 0) {
@@ -232,22 +274,10 @@ void tfdp_server::run() {
                 cv_done.notify_all();
             }
         }
-        // free the slots of released, drained jobs
-        for (auto it = jobs.begin(); it != jobs.end();) {
-            Job* j = it->second.get();
-            if (j->release && j->queue.empty() && j->admitted) {
-                tfdp_destroy_graph(j->g);
-                cudaEventDestroy(j->ev);
-                cudaStreamDestroy(j->stream);
-                used -= j->footprint;
-                --active;
-                cv_load.notify_all();
-                it = jobs.erase(it);
-            } else {
-                ++it;
-            }
-        }
     }
+    // stopping: let queued chunks finish before the jobs are destroyed
+    lk.unlock();
+    for (auto& jr : inflight) cudaEventSynchronize(jr.first->ev);
 }
 
 extern "C" {
@@ -331,6 +361,7 @@ tfdp_status tfdp_server_update(tfdp_server* s, int64_t job_id, const tfdp_params
     r.t_submit = now_s();
     j->queue.push_back(r);
     if (request_id) *request_id = r.id;
+    s->kick.store(true);
     s->cv_work.notify_all();
     return TFDP_OK;
 }
@@ -362,6 +393,7 @@ tfdp_status tfdp_server_release(tfdp_server* s, int64_t job_id) {
     auto it = s->jobs.find(job_id);
     if (it == s->jobs.end()) return TFDP_ERR_INVALID_ARG;
     it->second->release = true;
+    s->kick.store(true);
     s->cv_work.notify_all();
     return TFDP_OK;
 }

@@ -141,6 +141,13 @@ struct tfdp_graph {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
 
+    // failure detection: device flags read back by the synchronising calls (flags_word),
+    // every flag reported so far (flags_seen), and the test hooks of tfdp_debug_inject
+    unsigned flags_word = 0;
+    unsigned flags_seen = 0;
+    int inject_alloc_fail = 0;  // FFT-arena allocations still to refuse
+    int inject_scan_stall = 0;  // > 0: look-back poll limit with the first tile withheld
+
     // k of the next iteration (the fixed k, or the dynamic schedule's k at host_iter)
     int k_now() const { return k_of_iter(params.k_interp, host_iter, params.total_iters); }
 
@@ -304,6 +311,10 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     size_t o_tw = A.take(sizeof(float2) * P);
     void* mem = nullptr;
     CK(prepare_fft(logP));
+    if (g->inject_alloc_fail > 0) {  // test hook: refused as if the device were full
+        --g->inject_alloc_fail;
+        return cuda_fail(cudaErrorMemoryAllocation, "cudaMalloc(fft arena) [refused by tfdp_debug_inject]");
+    }
     cudaError_t e = cudaMalloc(&mem, A.bytes);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fft arena)");
     char* b = (char*)mem;
@@ -373,6 +384,8 @@ tfdp_status upload_params(tfdp_graph* g) {
     g->dp = make_dev_params(g->params, g->P ? g->P : 128, g->logP ? g->logP : 7);
     g->dp.step_table = g->step_table;
     g->dp.spread_shift = g->spread_shift;
+    g->dp.scan_spin_limit = g->inject_scan_stall;
+    g->dp.scan_stall = g->inject_scan_stall > 0 ? 1 : 0;
     CK(cudaMemcpyAsync(g->dprm, &g->dp, sizeof(DevParams), cudaMemcpyHostToDevice, g->stream));
     // dp lives in the graph object, which outlives the copy; the copy is ordered
     // before any later kernel on the stream.
@@ -414,6 +427,35 @@ tfdp_status fft_ready(tfdp_graph* g) {
     if (st != TFDP_OK) return st;
     CK(cudaStreamSynchronize(g->stream));
     return TFDP_OK;
+}
+
+// Status of device-side checks: a bounded wait that gave up is TFDP_ERR_TIMEOUT, any
+// other flag (a non-finite position, a box or sorted slot out of range) is
+// TFDP_ERR_DEVICE_CHECK.
+tfdp_status status_of_flags(unsigned f) {
+    if (f & FLAG_WAIT_TIMEOUT) return TFDP_ERR_TIMEOUT;
+    return f ? TFDP_ERR_DEVICE_CHECK : TFDP_OK;
+}
+
+// Wait for the graph's stream and report the device flags raised since the last report.
+// The flags are then cleared on the device (tfdp_get_stats keeps showing them); a flag
+// of the sort (a wait that ran out, a slot out of range) may have left the visit order
+// with repeated or missing nodes, so the order of the next iteration restarts from the
+// caller order.
+tfdp_status sync_checked(tfdp_graph* g) {
+    CK(cudaMemcpyAsync(&g->flags_word, &g->dst->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const unsigned f = g->flags_word;
+    if (!f) return TFDP_OK;
+    g->flags_seen |= f;
+    CK(cudaMemsetAsync(&g->dst->flags, 0, sizeof(unsigned), g->stream));
+    if ((f & (FLAG_WAIT_TIMEOUT | FLAG_SORT_RANGE | FLAG_BOX_RANGE)) && g->fft_mem && g->n > 0) {
+        const int slot = (int)(g->host_iter & 1);
+        CK(launch_order_reset(g->node_launch(), slot, g->stream));
+        g->order_valid[slot] = true;
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    return status_of_flags(f);
 }
 
 // Enqueue one iteration (advance = 1) or one force evaluation (advance = 0, eval = 1).
@@ -785,8 +827,7 @@ tfdp_status tfdp_get_positions(tfdp_graph* g, float* xy, int on_device) {
         CK(cudaMemcpyAsync(xy, g->xy[slot], sizeof(float2) * (size_t)g->n,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->stream));
     }
-    CK(cudaStreamSynchronize(g->stream));
-    return TFDP_OK;
+    return sync_checked(g);
 }
 
 tfdp_status tfdp_iterate(tfdp_graph* g, int32_t iters) {
@@ -834,8 +875,7 @@ tfdp_status tfdp_run(tfdp_graph* g, const float* xy_in, int32_t iters, float* xy
     if (st != TFDP_OK) return st;
     const int slot = (int)(g->host_iter & 1);
     CK(cudaMemcpyAsync(xy_out, g->xy[slot], sizeof(float2) * (size_t)g->n, cudaMemcpyDeviceToHost, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    return TFDP_OK;
+    return sync_checked(g);
 }
 
 tfdp_status tfdp_set_iteration(tfdp_graph* g, int64_t t) {
@@ -864,8 +904,7 @@ tfdp_status tfdp_eval_forces(tfdp_graph* g, float* frep, float* fatt, int on_dev
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (frep) CK(cudaMemcpyAsync(frep, g->frep_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
     if (fatt) CK(cudaMemcpyAsync(fatt, g->fatt_buf, sizeof(float2) * (size_t)g->n, kind, g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    return TFDP_OK;
+    return sync_checked(g);
 }
 
 tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
@@ -883,7 +922,7 @@ tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
     out->grid_G = s.grid.G;
     out->fft_P = g->P;
     out->spectrum_builds = s.spec_builds;
-    out->device_flags = (int32_t)s.flags;
+    out->device_flags = (int32_t)(s.flags | g->flags_seen);
     out->kernels_per_iteration = kernels_per_iteration(g);
     out->grid_k = s.grid.k;
     return TFDP_OK;
@@ -972,8 +1011,26 @@ tfdp_status tfdp_get_stage_times(tfdp_graph* g, float* ms, int nstages) {
 
 tfdp_status tfdp_synchronize(tfdp_graph* g) {
     if (!g) return TFDP_ERR_INVALID_ARG;
-    CK(cudaStreamSynchronize(g->stream));
-    return TFDP_OK;
+    return sync_checked(g);
+}
+
+tfdp_status tfdp_debug_inject(tfdp_graph* g, int what, int value) {
+    if (!g || value < 0) return TFDP_ERR_INVALID_ARG;
+    switch (what) {
+        case TFDP_INJECT_FFT_ALLOC:
+            g->inject_alloc_fail = value;
+            return TFDP_OK;
+        case TFDP_INJECT_SCAN_STALL: {
+            CK(cudaStreamSynchronize(g->stream));  // no queued iteration reads the old parameters
+            g->inject_scan_stall = value;
+            tfdp_status st = upload_params(g);
+            if (st != TFDP_OK) return st;
+            CK(cudaStreamSynchronize(g->stream));
+            return TFDP_OK;
+        }
+        default:
+            return TFDP_ERR_INVALID_ARG;
+    }
 }
 
 tfdp_status tfdp_graph_set_stream(tfdp_graph* g, void* stream) {

@@ -19,6 +19,8 @@ GRID_PAPER, GRID_SNAP_H = 0, 1
 K_DYNAMIC = 0  # k_interp: the dynamic k schedule (1, then 2, then 3)
 WEIGHT_MAX = 64.0  # largest local-refinement weight
 DEBUG_GRID_CHARGES, DEBUG_GRID_OUTPUT, DEBUG_SORT_PERM, DEBUG_CELL_START = 1, 2, 3, 4
+INJECT_FFT_ALLOC, INJECT_SCAN_STALL = 1, 2  # failure-detection test hooks (tfdp_debug_inject)
+FLAG_NONFINITE, FLAG_BOX_RANGE, FLAG_SORT_RANGE, FLAG_WAIT_TIMEOUT = 1, 2, 4, 8  # device_flags bits
 STAGES = ["sort", "spread", "spectrum", "rows_fwd", "cols", "rows_inv", "gather_update",
           "exact", "edge_update", "attract"]
 
@@ -84,6 +86,7 @@ _SIGS = {
     "tfdp_get_stage_times": ([_p, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
     "tfdp_destroy_graph": ([_p], ctypes.c_int),
     "tfdp_debug_fetch": ([_p, ctypes.c_int, _p, ctypes.c_size_t], ctypes.c_int),
+    "tfdp_debug_inject": ([_p, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "tfdp_exact_repulsion_noalloc": ([_p, ctypes.c_int64, ctypes.c_double, _p, _p], ctypes.c_int),
     "tfdp_batch_create": ([ctypes.c_int32, _p, _p, _p, _p, _p, _p, ctypes.POINTER(_p)], ctypes.c_int),
     "tfdp_batch_iterate": ([_p, ctypes.c_int32], ctypes.c_int),
@@ -309,6 +312,10 @@ class Graph:
 
     def synchronize(self):
         _check(lib.tfdp_synchronize(self._h), "tfdp_synchronize")
+
+    def debug_inject(self, what, value):
+        """Failure-detection test hook (INJECT_FFT_ALLOC / INJECT_SCAN_STALL, see tfdp.h)."""
+        _check(lib.tfdp_debug_inject(self._h, int(what), int(value)), "tfdp_debug_inject")
 
     def debug_fetch(self, what):
         s = self.stats()
