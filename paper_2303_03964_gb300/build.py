@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtfdp.so")
 SOURCES = ["tfdp_api.cu", "node_kernels.cu", "fft_kernels.cu", "batch.cu", "batch_k1.cu", "batch_k2.cu",
-           "batch_k3.cu", "server.cu", "noalloc.cu"]
+           "batch_k3.cu", "server.cu", "noalloc.cu", "cols_tc.cu"]
 HEADERS = ["common.cuh", "fft.cuh", "fft_reg.cuh", "fft_stages.cuh", "node_dev.cuh", "launch.h", "batch_kernel.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

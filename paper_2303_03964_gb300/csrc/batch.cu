@@ -225,6 +225,7 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
         p.rep_mode = TFDP_REP_FFT;
         tfdp_status st = tfdp_params_check(&p, nullptr);
         if (st == TFDP_OK && p.k_interp == TFDP_K_DYNAMIC) st = TFDP_ERR_PARAM_RANGE;  // one fixed k per batch
+        if (st == TFDP_OK && p.precision != TFDP_PREC_FP32) st = TFDP_ERR_PARAM_RANGE;  // FP32 kernels only
         if (st != TFDP_OK || (g > 0 && p.k_interp != b->params[0].k_interp) || n[g] < 1 || m[g] < 0 ||
             (m[g] > 0 && !edges[g]) || !xy0[g]) {
             delete b;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace tfdp {
@@ -33,6 +35,14 @@ cudaError_t launch_rows_fwd(const FftLaunch& a, cudaStream_t s);   // 1 kernel
 cudaError_t launch_cols(const FftLaunch& a, cudaStream_t s);       // 1 kernel
 cudaError_t launch_rows_inv(const FftLaunch& a, cudaStream_t s);   // 1 kernel
 int fft_rows_per_cta(int logP);
+// BF16x3 tensor-core column stage (cols_tc.cu), P = 2048 only: the 96 KB DFT-matrix image
+// (build_tc_constants, uploaded once per arena), natural-order kernel spectra
+// (3 x (P/2+1) x P floats, rebuilt in place when the spectrum is stale), 1 kernel.
+void build_tc_constants(std::vector<unsigned char>& img);
+size_t tc_constants_bytes();
+size_t tc_spectrum_floats();
+cudaError_t prepare_cols_tc();  // shared-memory attribute (call outside stream capture)
+cudaError_t launch_cols_tc(const FftLaunch& a, const unsigned char* consts, float* specN, cudaStream_t s);
 // Shared-memory attributes of the FFT kernels of size 2^logP (call outside stream capture).
 cudaError_t prepare_fft(int logP);
 

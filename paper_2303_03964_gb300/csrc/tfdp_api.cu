@@ -122,6 +122,9 @@ struct tfdp_graph {
     float* specHx = nullptr;
     float* specHy = nullptr;
     float2* tw = nullptr;
+    // BF16x3 tensor-core column stage: DFT-matrix image and natural-order spectra
+    unsigned char* tc_consts = nullptr;
+    float* specN = nullptr;
 
     // captured iterations
     // captured iterations, one pair (1 and kBatchIters iterations) per k
@@ -278,7 +281,9 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     const int chunk = scan_items_per_block();
     const int scan_blocks = (nbox_max + chunk - 1) / chunk;
     if (scan_blocks > 1024) return TFDP_ERR_PARAM_RANGE;
-    if (g->fft_mem && g->P == P && g->nbox_max == nbox_max && g->G_max == G_max) return TFDP_OK;
+    const bool tc = g->params.precision == TFDP_PREC_BF16X3;
+    if (g->fft_mem && g->P == P && g->nbox_max == nbox_max && g->G_max == G_max && (!tc || g->tc_consts))
+        return TFDP_OK;
     if (g->fft_mem) {
         CK(cudaStreamSynchronize(g->stream));
         CK(cudaFree(g->fft_mem));
@@ -309,8 +314,11 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     size_t o_sHx = A.take(sizeof(float) * NH * P);
     size_t o_sHy = A.take(sizeof(float) * NH * P);
     size_t o_tw = A.take(sizeof(float2) * P);
+    size_t o_tcc = tc ? A.take(tc_constants_bytes()) : 0;
+    size_t o_spn = tc ? A.take(sizeof(float) * tc_spectrum_floats()) : 0;
     void* mem = nullptr;
     CK(prepare_fft(logP));
+    if (tc) CK(prepare_cols_tc());
     if (g->inject_alloc_fail > 0) {  // test hook: refused as if the device were full
         --g->inject_alloc_fail;
         return cuda_fail(cudaErrorMemoryAllocation, "cudaMalloc(fft arena) [refused by tfdp_debug_inject]");
@@ -337,6 +345,8 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->specHx = (float*)(b + o_sHx);
     g->specHy = (float*)(b + o_sHy);
     g->tw = (float2*)(b + o_tw);
+    g->tc_consts = tc ? (unsigned char*)(b + o_tcc) : nullptr;
+    g->specN = tc ? (float*)(b + o_spn) : nullptr;
     g->P = P;
     g->logP = logP;
     g->G_max = G_max;
@@ -356,9 +366,14 @@ tfdp_status alloc_fft(tfdp_graph* g) {
         tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
     CK(cudaMemcpyAsync(g->tw, tw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, g->stream));
+    std::vector<unsigned char> tcimg;
+    if (tc) {
+        build_tc_constants(tcimg);
+        CK(cudaMemcpyAsync(g->tc_consts, tcimg.data(), tcimg.size(), cudaMemcpyHostToDevice, g->stream));
+    }
     // a new arena has no valid spectrum
     CK(cudaMemsetAsync(&g->dst->spec_valid, 0, sizeof(int), g->stream));
-    CK(cudaStreamSynchronize(g->stream));  // keeps `tw` alive until copied
+    CK(cudaStreamSynchronize(g->stream));  // keeps `tw` and `tcimg` alive until copied
     return TFDP_OK;
 }
 
@@ -516,7 +531,8 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval, i
         CK(launch_rows_fwd(f, s));
         CK(end(TFDP_STAGE_ROWS_FWD, s));
         CK(begin(TFDP_STAGE_COLS, s));
-        CK(launch_cols(f, s));
+        if (g->params.precision == TFDP_PREC_BF16X3) CK(launch_cols_tc(f, g->tc_consts, g->specN, s));
+        else CK(launch_cols(f, s));
         CK(end(TFDP_STAGE_COLS, s));
         CK(begin(TFDP_STAGE_ROWS_INV, s));
         CK(launch_rows_inv(f, s));
@@ -544,7 +560,8 @@ int kernels_per_iteration(const tfdp_graph* g) {
 long long exec_key_of(const tfdp_graph* g, int k) {
     return ((long long)g->params.rep_mode << 40) | ((long long)k << 32) |
            ((long long)g->dp.gamma_int << 24) | ((long long)g->logP << 16) |
-           ((long long)g->timing_mask << 48) | (long long)(g->fft_mem != nullptr);
+           ((long long)g->timing_mask << 48) | ((long long)g->params.precision << 60) |
+           (long long)(g->fft_mem != nullptr);
 }
 
 // Capture `iters` iterations with the kernels of interpolation order k.
@@ -636,7 +653,7 @@ tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
     if (p->grid_max < (p->k_interp ? p->k_interp : kMaxK)) return TFDP_ERR_PARAM_RANGE;
     if (p->grid_policy != TFDP_GRID_PAPER && p->grid_policy != TFDP_GRID_SNAP_H) return TFDP_ERR_INVALID_ARG;
     if (p->rep_mode != TFDP_REP_EXACT && p->rep_mode != TFDP_REP_FFT) return TFDP_ERR_INVALID_ARG;
-    if (p->precision != TFDP_PREC_FP32) return TFDP_ERR_PARAM_RANGE;  // BF16X3: not built
+    if (p->precision != TFDP_PREC_FP32 && p->precision != TFDP_PREC_BF16X3) return TFDP_ERR_INVALID_ARG;
     if (!(p->step_min > 0.0) || !(p->step0 >= p->step_min) || !std::isfinite(p->step0)) return TFDP_ERR_PARAM_RANGE;
     if (p->total_iters < 1) return TFDP_ERR_PARAM_RANGE;
     for (int i = 0; i < 7; ++i)
@@ -645,6 +662,8 @@ tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
         int P, l, G, nb;
         if (!fft_geometry(*p, &P, &l, &G, &nb)) return TFDP_ERR_PARAM_RANGE;
         if ((nb + scan_items_per_block() - 1) / scan_items_per_block() > 1024) return TFDP_ERR_PARAM_RANGE;
+        // the tensor-core column stage is built for the 64 x 32 factorisation of P = 2048
+        if (p->precision == TFDP_PREC_BF16X3 && P != 2048) return TFDP_ERR_PARAM_RANGE;
     }
     if (weight_ok) *weight_ok = (p->alpha * (1.0 + p->beta) < 1.0) ? 1 : 0;
     return TFDP_OK;
@@ -789,7 +808,10 @@ tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
     tfdp_status st = tfdp_params_check(p, nullptr);
     if (st != TFDP_OK) return st;
     const bool to_fft = p->rep_mode == TFDP_REP_FFT && g->params.rep_mode != TFDP_REP_FFT;
+    const bool prec_changed = p->precision != g->params.precision;
     g->params = *p;
+    if (prec_changed && g->dst)  // each precision mode keeps its own spectrum arrays
+        CK(cudaMemsetAsync(&g->dst->spec_valid, 0, sizeof(int), g->stream));
     if (p->rep_mode == TFDP_REP_FFT) {
         void* before = g->fft_mem;
         st = alloc_fft(g);

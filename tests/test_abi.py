@@ -104,3 +104,18 @@ def test_noalloc_rejects_null_and_size_before_any_launch():
     big = tfdp.NOALLOC_MAX_N + 1
     assert tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(0x1000), big, 2.0, tfdp._p(0x2000), None) == 3
     assert tfdp.lib.tfdp_exact_repulsion_noalloc(tfdp._p(0x1000), 10, 1.0, tfdp._p(0x2000), None) == 3
+
+
+def test_bf16x3_precision_mode_accepted_only_at_its_fft_size():
+    # the tensor-core column stage is built for P = 2048 (grid_max 513 .. 1024)
+    assert tfdp.params_check(tfdp.params_default(precision=tfdp.PREC_BF16X3, grid_max=1023)) is True
+    for gm in (255, 511, 2047):
+        with pytest.raises(tfdp.TfdpError) as ei:
+            tfdp.params_check(tfdp.params_default(precision=tfdp.PREC_BF16X3, grid_max=gm))
+        assert ei.value.status == 3
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.params_check(tfdp.params_default(precision=7))
+    assert ei.value.status == 1
+    # the exact path has no grid convolution: the mode is accepted and changes nothing
+    assert tfdp.params_check(tfdp.params_default(precision=tfdp.PREC_BF16X3, rep_mode=tfdp.REP_EXACT,
+                                                 grid_max=255)) is True

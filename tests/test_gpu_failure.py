@@ -44,7 +44,7 @@ def _oracle_fft(xy32, P, k=3, grid_max=1023):
 def test_scan_wait_that_runs_out_is_reported_as_timeout(tfdp):
     rng = synth.rng_for(61)
     n = 40_000  # side 200: N_int = 200, 40,000 boxes, 20 scan tiles
-    e = synth.sbm(n, 10, 8.0, 0.9, rng)
+    e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
     xy = synth.uniform_positions(n, 100.0, rng)
     with tfdp.Graph(n, e, xy, tfdp.params_default(grid_max=1023, total_iters=50)) as g:
         g.iterate(2)
@@ -70,7 +70,7 @@ def test_scan_wait_that_runs_out_is_reported_as_timeout(tfdp):
 def test_refused_fft_allocation_is_retried_and_never_launches_without_buffers(tfdp):
     rng = synth.rng_for(63)
     n = 5_000
-    e = synth.sbm(n, 10, 8.0, 0.9, rng)
+    e, _ = synth.sbm(n, 10, 8.0, 0.9, rng)
     xy = synth.uniform_positions(n, 60.0, rng)
     with tfdp.Graph(n, e, xy, tfdp.params_default(grid_max=255, total_iters=50)) as g:
         g.iterate(2)
