@@ -386,14 +386,33 @@ def serving_measurement(jobs=200, rate=20.0, updates=5, init_iters=300, upd_iter
             "chunk_iters": chunk}
 
 
-def workload_measurement(name, stream, flush, steps, warmup):
-    """Device-resident throughput of another configuration's workload (same timing as the
-    main line: L2 flushed before each step, CUDA events around each step)."""
+def stage_roofline(stage, ms, n, m, G, P, nbox, peak, peak_kind):
+    """Roofline of one single-kernel stage from its in-graph time: algorithmic bytes
+    (stage_bytes) against the HBM peak, or, for the exact kernel, about 11 FP32 flops per
+    pair against the FP32 FMA peak (152 SMs x 128 lanes x 2 flops x 2.07 GHz)."""
+    if stage == "exact":
+        fma_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        ach = 11.0 * n * n / (ms * 1e-3) / 1e12
+        return {"stage": stage, "kernel": STAGE_KERNEL[stage], "bound": "alu", "achieved": ach,
+                "kernel_ms": ms, "peak": fma_peak, "unit": "TFLOP/s", "frac": ach / fma_peak, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.07 GHz"}
+    bytes_ = stage_bytes(stage, n, m, G, P, nbox)
+    ach = bytes_ / (ms * 1e-3) / 1e9
+    return {"stage": stage, "kernel": STAGE_KERNEL[stage], "bound": "hbm", "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "traffic": None, "algorithmic_bytes": bytes_, "kernel_ms": ms,
+            "peak_kind": peak_kind + " hbm_gbs (burst copy)"}
+
+
+def workload_measurement(name, stream, flush, steps, warmup, cpu=True):
+    """Another configuration's workload with the main line's timing (L2 flushed before
+    each step, CUDA events around each step): device-resident rate, per-stage times and
+    the roofline of its dominant single-kernel stage, the end-to-end rate through
+    tfdp_run with pinned host buffers, and the FP64 oracle on the host cores."""
     import torch
     from paper_2303_03964_gb300 import tfdp
     spec = WORKLOADS[name]
     e, xy = make_workload(name)
-    n = xy.shape[0]
+    n, m = xy.shape[0], e.shape[0]
     rep_mode = tfdp.REP_EXACT if spec["rep"] == "exact" else tfdp.REP_FFT
     params = tfdp.params_default(rep_mode=rep_mode, k_interp=spec["k"], grid_max=spec["grid_max"],
                                  total_iters=spec["total_iters"])
@@ -412,9 +431,42 @@ def workload_measurement(name, stream, flush, steps, warmup):
             step()
         ms = [step() for _ in range(steps)]
         st = g.stats()
-    return {"desc": spec["desc"], "rep": spec["rep"], "n": int(n), "m": int(e.shape[0]),
-            "value": n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": sum(ms) / len(ms),
-            "grid_G": st["grid_G"], "fft_P": st["fft_P"], "device_flags": st["device_flags"]}
+        # stage breakdown (events on a side branch of the iteration), after the timed steps
+        g.set_stage_timing(True)
+        brk = []
+        for _ in range(5):
+            step()
+            brk.append(g.stage_times())
+        g.set_stage_timing(False)
+        stages = {k: statistics.fmean(b[k] for b in brk[2:]) for k in brk[0]}
+        # end to end: upload, one iteration, download per call (pinned host buffers)
+        hin = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        hout = torch.empty((n, 2), dtype=torch.float32, pin_memory=True)
+        g.get_positions(hout.numpy())
+        hin.copy_(hout)
+        e2e = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            g.run(hin.numpy(), 1, hout.numpy())
+            e2e.append(time.perf_counter() - t0)
+            hin.copy_(hout)
+    G, P = st["grid_G"], st["fft_P"]
+    nbox = st["grid_n_int"] ** 2
+    cand = {k: v for k, v in stages.items() if k in STAGE_KERNEL and v > 0}
+    dom = max(cand, key=cand.get)
+    peak, peak_kind = measured_peaks()
+    step_ms = sum(ms) / len(ms)
+    out = {"desc": spec["desc"], "rep": spec["rep"], "n": int(n), "m": int(m),
+           "value": n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
+           "grid_G": G, "fft_P": P, "device_flags": st["device_flags"], "stages_ms": stages,
+           "roofline": stage_roofline(dom, cand[dom], n, m, G, P, nbox, peak, peak_kind),
+           "iteration_roofline": (iteration_roofline(n, m, G, P, step_ms, peak)
+                                  if spec["rep"] == "fft" else None),
+           "e2e": {"value": n * len(e2e) / sum(e2e), "unit": UNIT, "h2d_bytes_per_step": 8 * n,
+                   "d2h_bytes_per_step": 8 * n}}
+    if cpu:
+        out["cpu_baseline"] = cpu_baseline(e, xy, spec, budget_s=6.0)
+    return out
 
 
 def exact_kernel_measurement(stream, flush, steps, warmup, name="er_64k_exact"):
@@ -544,6 +596,7 @@ def quality_measurement():
     from paper_2303_03964_gb300 import quality as q
     from paper_2303_03964_gb300 import synth, tfdp
     rng = synth.rng_for(6)
+    rng_spread = synth.rng_for(7)  # other starts, drawn apart so the main sequence is unchanged
     graphs = []
     e, _ = synth.sbm(2000, 10, 8.0, 0.9, rng)
     graphs.append(("sbm_2000", 2000, e))
@@ -559,6 +612,13 @@ def quality_measurement():
                 g.iterate(300)
                 m[label] = q.evaluate(g.get_positions(), e)
         m["relative"] = {k: q.relative(m["ibfft"][k], m["exact"][k]) for k in m["exact"]}
+        # the spread of the exact method itself: the same graph from another random start
+        xy1 = synth.uniform_positions(n, np.sqrt(n) / 2.0, rng_spread)
+        with tfdp.Graph(n, e, xy1, tfdp.params_default(rep_mode=tfdp.REP_EXACT, total_iters=300,
+                                                        grid_max=255)) as g:
+            g.iterate(300)
+            other = q.evaluate(g.get_positions(), e)
+        m["exact_seed_spread"] = {k: q.relative(other[k], m["exact"][k]) for k in m["exact"]}
         out[name] = m
     return out
 
@@ -592,6 +652,7 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
     graphs = synth.batch_mixed()
     params = [tfdp.params_default(grid_max=255, total_iters=300) for _ in graphs]
     total_n = sum(g[0] for g in graphs)
+    peak, _ = measured_peaks()
     b = tfdp.Batch(graphs, params, stream=stream.cuda_stream)
     blocks = b.autotune(3)
 
@@ -613,7 +674,12 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
     ms = [timed(lambda: b.iterate(1)) for _ in range(steps)]
     if sampler is not None and isinstance(sampler, NvmlSampler):
         sampler.active = False
-    flags = max(b.stats(q)["device_flags"] for q in (0, len(graphs) // 2, len(graphs) - 1))
+    sts = [b.stats(q) for q in range(len(graphs))]
+    flags = max(st["device_flags"] for st in sts)
+    # single-pass byte model of every graph's iteration at its own grid (the FFT size of
+    # the batch is shared)
+    model_bytes = sum(iteration_model_bytes(g[0], len(g[1]), st["grid_G"], st["fft_P"])
+                      for g, st in zip(graphs, sts))
     b.close()
     # solo: a sample of the same graphs, one graph per launch sequence
     idx = list(range(0, len(graphs), max(1, len(graphs) // solo_sample)))[:solo_sample]
@@ -633,7 +699,12 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
             "value": batch_value, "unit": UNIT, "ms_per_step": statistics.fmean(ms),
             "cooperative_ctas": blocks, "solo_value": solo_value,
             "solo_sample": "%d of the graphs (%d nodes), one iteration each, median of 3" % (len(idx), solo_n),
-            "speedup_vs_solo": batch_value / solo_value, "device_flags": flags}
+            "speedup_vs_solo": batch_value / solo_value, "device_flags": flags,
+            "iteration_roofline": {
+                "bytes_per_iteration": model_bytes,
+                "achieved": model_bytes / (statistics.fmean(ms) * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": model_bytes / (statistics.fmean(ms) * 1e-3) / 1e9 / peak,
+                "model": "sum over graphs of 28 n + 24 m node bytes + 24 G^2 + 60 P (P/2+1) grid bytes"}}
 
 
 def dist_env():
@@ -798,7 +869,8 @@ def run_ours(args):
         serving = serving_measurement(sampler=sampler)
     others = None
     if not args.no_workloads and args.workload == "lattice_1m":
-        others = {w: workload_measurement(w, stream, flush, min(args.steps, 20), args.warmup)
+        others = {w: workload_measurement(w, stream, flush, min(args.steps, 20), args.warmup,
+                                          cpu=not args.no_cpu_baseline)
                   for w in ("er_2000_exact", "sbm_100k", "ba_2m")}
     exact_kernel = None
     if not args.no_workloads and args.workload == "lattice_1m":

@@ -37,12 +37,17 @@ def relative():
     return rel
 
 
-def test_each_graph_within_ten_percent(relative):
+def test_each_graph_within_six_percent(relative):
+    # A single layout is one trajectory of a chaotic iteration: two exact layouts of the
+    # same graph from two random starts differ by a few percent as well (the bench
+    # quality line reports that spread), so the per-graph bound sits above the paper's
+    # 4 % band, which is a statement about the mean.
     for r in relative:
         for k in METRICS:
-            assert abs(r[k]) <= 0.10, (k, r)
+            assert abs(r[k]) <= 0.06, (k, r)
 
 
-def test_mean_over_graphs_near_zero(relative):
+def test_mean_over_graphs_within_paper_band(relative):
+    # Sec. 4.2: relative values within [-4 %, +4 %], mean near zero
     for k in METRICS:
-        assert abs(np.mean([r[k] for r in relative])) <= 0.05, k
+        assert abs(np.mean([r[k] for r in relative])) <= 0.04, k
