@@ -494,8 +494,12 @@ int or_iterate(int64_t n, int64_t m, const int32_t* edges, double* xy, const dou
         } else {
             for (int64_t i = 0; i < 2 * n; ++i) xyf[i] = (float)xy[i];
             const int kt = or_k_of_iter(k, t, T);
+            /* Under the dynamic strategy N_int has one cap for every k, floor(grid_max / 3):
+             * the paper's N_int rule (Sec. 3.4 "Choices of k") does not depend on k, so the
+             * k = 1 grid is a third of the k = 3 grid per axis (reading R9b). */
+            const int gm = (k == 0) ? kt * (grid_max / 3) : grid_max;
             double g[5];
-            or_grid_policy(n, xyf, kt, n_int_min, grid_max, policy, g);
+            or_grid_policy(n, xyf, kt, n_int_min, gm, policy, g);
             int n_int = (int)g[2];
             int64_t PP = P > 0 ? P : or_nextpow2(2 * (int64_t)n_int * kt - 1);
             rc = or_rep_fft(n, xy, xyf, wr, gamma, kt, g[0], g[1], n_int, PP, frep);

@@ -386,17 +386,33 @@ def test_dynamic_k_schedule_counts(paper):
 
 def test_dynamic_k_iteration_is_the_fixed_k_segments():
     """A dynamic-k run equals fixed-k runs chained at the schedule's boundaries (T = 20:
-    k = 1 for t < 18, k = 2 at t = 18, k = 3 at t = 19)."""
+    k = 1 for t < 18, k = 2 at t = 18, k = 3 at t = 19). The paper's N_int rule does not
+    depend on k (Sec. 3.4 "Choices of k"), so under the dynamic strategy N_int has one
+    cap, floor(grid_max / 3), and the fixed-k segment of order k runs with a cap of
+    k * floor(grid_max / 3) on G (reading R9b)."""
     e, xy = _random_graph(60, 150, 7)
     xy = xy * 6.0
-    kw = dict(mode="fft", n_int_min=4, grid_max=30, T=20, alpha=0.1, beta=8.0, gamma=2.0)
-    dyn = oracle.iterate(xy, e, 20, k=0, **kw)
-    x = oracle.iterate(xy, e, 18, k=1, t0=0, **kw)
-    x = oracle.iterate(x, e, 1, k=2, t0=18, **kw)
-    x = oracle.iterate(x, e, 1, k=3, t0=19, **kw)
+    kw = dict(mode="fft", n_int_min=4, T=20, alpha=0.1, beta=8.0, gamma=2.0)
+    gm = 30
+    L = float(np.float32(xy).max() - np.float32(xy).min())
+    assert L > gm // 3  # the common cap binds, so the rule is visible
+    dyn = oracle.iterate(xy, e, 20, k=0, grid_max=gm, **kw)
+    x = oracle.iterate(xy, e, 18, k=1, t0=0, grid_max=1 * (gm // 3), **kw)
+    x = oracle.iterate(x, e, 1, k=2, t0=18, grid_max=2 * (gm // 3), **kw)
+    x = oracle.iterate(x, e, 1, k=3, t0=19, grid_max=3 * (gm // 3), **kw)
     assert np.array_equal(dyn, x)
     # and differs from a fixed-k run, so the switch is not a no-op
-    assert not np.array_equal(dyn, oracle.iterate(xy, e, 20, k=3, **kw))
+    assert not np.array_equal(dyn, oracle.iterate(xy, e, 20, k=3, grid_max=gm, **kw))
+    # a cap of floor(grid_max / k) per k (the k = 1 grid as wide as the k = 3 grid) is
+    # another run
+    y = oracle.iterate(xy, e, 18, k=1, t0=0, grid_max=gm, **kw)
+    y = oracle.iterate(y, e, 1, k=2, t0=18, grid_max=gm, **kw)
+    y = oracle.iterate(y, e, 1, k=3, t0=19, grid_max=gm, **kw)
+    assert not np.array_equal(dyn, y)
+    # one N_int for every k: the k = 1 grid is a third of the k = 3 grid per axis
+    g1 = oracle.grid_policy(np.float32(xy), 1, 4, 1 * (gm // 3))
+    g3 = oracle.grid_policy(np.float32(xy), 3, 4, 3 * (gm // 3))
+    assert g1["n_int"] == g3["n_int"] == gm // 3 and g3["G"] == 3 * g1["G"]
 
 
 # ------------------------------------------------------------------ local refinement
