@@ -146,7 +146,9 @@ __device__ __forceinline__ GridDesc make_grid(float lo_f, float hi_f, const DevP
     double c = ceil(L);
     if (c > 2.0e9) c = 2.0e9;
     int n_int = (c > (double)p.n_int_min) ? (int)c : p.n_int_min;
-    int cap = p.grid_max / k;
+    // N_int cap: floor(grid_max / k) for a fixed k; one cap, floor(grid_max / 3), for every
+    // k under the dynamic strategy (p.k = 0), whose N_int rule does not depend on k
+    int cap = p.grid_max / (p.k > 0 ? k : kMaxK);
     if (n_int > cap) n_int = cap;
     if (n_int < 1) n_int = 1;
     double h;

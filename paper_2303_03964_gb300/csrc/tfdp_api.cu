@@ -122,6 +122,11 @@ struct tfdp_graph {
     float* specHx = nullptr;
     float* specHy = nullptr;
     float2* tw = nullptr;
+    // per order k (1..3) of the iterations: FFT size, largest grid and twiddle table (all
+    // equal to the graph's own for a fixed k; smaller for k < 3 under the dynamic strategy)
+    int logP_k[kMaxK + 1] = {};
+    int Gmax_k[kMaxK + 1] = {};
+    float2* tw_k[kMaxK + 1] = {};
     // BF16x3 tensor-core column stage: DFT-matrix image and natural-order spectra
     unsigned char* tc_consts = nullptr;
     float* specN = nullptr;
@@ -189,10 +194,10 @@ struct tfdp_graph {
         a.fatt_out = fatt_buf;
         return a;
     }
-    FftLaunch fft_launch() const {
+    FftLaunch fft_launch(int k) const {
         FftLaunch f{};
-        f.logP = logP;
-        f.G_max = G_max;
+        f.logP = logP_k[k];
+        f.G_max = Gmax_k[k];
         f.Gs = Gs;
         f.ystride = ystride;
         f.gin = gin;
@@ -203,7 +208,7 @@ struct tfdp_graph {
         f.specK = specK;
         f.specHx = specHx;
         f.specHy = specHy;
-        f.tw = tw;
+        f.tw = tw_k[k];
         f.st = dst;
         f.prm = dprm;
         return f;
@@ -251,11 +256,12 @@ DevParams make_dev_params(const tfdp_params& p, int P, int logP) {
 // FFT geometry implied by the parameters: the largest grid and box count over the k
 // the graph can use (all of 1..3 under the dynamic schedule; k = 1 has the most boxes).
 bool fft_geometry(const tfdp_params& p, int* P, int* logP, int* G_max, int* nbox_max) {
-    const int k_lo = p.k_interp ? p.k_interp : 1, k_hi = p.k_interp ? p.k_interp : kMaxK;
-    const int n_int_max = p.grid_max / k_lo;
-    if (p.grid_max / k_hi < 1) return false;
-    int G = 0;
-    for (int k = k_lo; k <= k_hi; ++k) G = std::max(G, (p.grid_max / k) * k);
+    // N_int is capped at floor(grid_max / k) for a fixed k; under the dynamic strategy one
+    // cap, floor(grid_max / 3), holds for every k (reading R9b), so G = k N_int <= grid_max
+    const int kcap = p.k_interp ? p.k_interp : kMaxK;
+    const int n_int_max = p.grid_max / kcap;
+    if (n_int_max < 1) return false;
+    const int G = kcap * n_int_max;
     int l = log2_ceil(2LL * G - 1);
     if (l < kMinLogP) l = kMinLogP;
     if (l > kMaxLogP) return false;
@@ -263,6 +269,25 @@ bool fft_geometry(const tfdp_params& p, int* P, int* logP, int* G_max, int* nbox
     *P = 1 << l;
     *G_max = G;
     *nbox_max = n_int_max * n_int_max;
+    return true;
+}
+
+// FFT size and largest grid of the iterations of order k (1..3): the graph's own for a
+// fixed k; under the dynamic strategy G <= k floor(grid_max / 3), so k = 1 and 2 run
+// smaller transforms than k = 3.
+bool fft_geometry_k(const tfdp_params& p, int k, int* logP, int* G_max) {
+    int P, l, G, nb;
+    if (!fft_geometry(p, &P, &l, &G, &nb)) return false;
+    if (p.k_interp) {
+        *logP = l;
+        *G_max = G;
+        return true;
+    }
+    const int Gk = k * (p.grid_max / kMaxK);
+    int lk = log2_ceil(2LL * Gk - 1);
+    if (lk < kMinLogP) lk = kMinLogP;
+    *logP = lk;
+    *G_max = Gk;
     return true;
 }
 
@@ -314,10 +339,17 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     size_t o_sHx = A.take(sizeof(float) * NH * P);
     size_t o_sHy = A.take(sizeof(float) * NH * P);
     size_t o_tw = A.take(sizeof(float2) * P);
+    int lk[kMaxK + 1] = {}, gk[kMaxK + 1] = {};
+    size_t o_twk[kMaxK + 1] = {};
+    for (int k = 1; k <= kMaxK; ++k) {
+        if (!fft_geometry_k(g->params, k, &lk[k], &gk[k])) return TFDP_ERR_PARAM_RANGE;
+        o_twk[k] = A.take(sizeof(float2) * ((size_t)1 << lk[k]));
+    }
     size_t o_tcc = tc ? A.take(tc_constants_bytes()) : 0;
     size_t o_spn = tc ? A.take(sizeof(float) * tc_spectrum_floats()) : 0;
     void* mem = nullptr;
     CK(prepare_fft(logP));
+    for (int k = 1; k <= kMaxK; ++k) CK(prepare_fft(lk[k]));
     if (tc) CK(prepare_cols_tc());
     if (g->inject_alloc_fail > 0) {  // test hook: refused as if the device were full
         --g->inject_alloc_fail;
@@ -345,6 +377,11 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     g->specHx = (float*)(b + o_sHx);
     g->specHy = (float*)(b + o_sHy);
     g->tw = (float2*)(b + o_tw);
+    for (int k = 1; k <= kMaxK; ++k) {
+        g->tw_k[k] = (float2*)(b + o_twk[k]);
+        g->logP_k[k] = lk[k];
+        g->Gmax_k[k] = gk[k];
+    }
     g->tc_consts = tc ? (unsigned char*)(b + o_tcc) : nullptr;
     g->specN = tc ? (float*)(b + o_spn) : nullptr;
     g->P = P;
@@ -366,6 +403,16 @@ tfdp_status alloc_fft(tfdp_graph* g) {
         tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
     }
     CK(cudaMemcpyAsync(g->tw, tw.data(), sizeof(float2) * P, cudaMemcpyHostToDevice, g->stream));
+    std::vector<float2> twk[kMaxK + 1];
+    for (int k = 1; k <= kMaxK; ++k) {
+        const int Pk = 1 << lk[k];
+        twk[k].resize((size_t)Pk);
+        for (int t = 0; t < Pk; ++t) {
+            const double a = -2.0 * pi * (double)t / (double)Pk;
+            twk[k][(size_t)t] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        CK(cudaMemcpyAsync(g->tw_k[k], twk[k].data(), sizeof(float2) * Pk, cudaMemcpyHostToDevice, g->stream));
+    }
     std::vector<unsigned char> tcimg;
     if (tc) {
         build_tc_constants(tcimg);
@@ -373,7 +420,7 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     }
     // a new arena has no valid spectrum
     CK(cudaMemsetAsync(&g->dst->spec_valid, 0, sizeof(int), g->stream));
-    CK(cudaStreamSynchronize(g->stream));  // keeps `tw` and `tcimg` alive until copied
+    CK(cudaStreamSynchronize(g->stream));  // keeps `tw`, `twk` and `tcimg` alive until copied
     return TFDP_OK;
 }
 
@@ -509,7 +556,7 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval, i
         CK(launch_edge_update(a, advance, eval, s));
         CK(end(TFDP_STAGE_EDGE_UPDATE, s));
     } else {
-        const FftLaunch f = g->fft_launch();
+        const FftLaunch f = g->fft_launch(k);
         CK(begin(TFDP_STAGE_SORT, s));
         CK(launch_fft_grid(a, advance, s));
         // attraction on the side stream, overlapping sort, spread and FFT
@@ -554,7 +601,9 @@ int kernels_per_iteration(const tfdp_graph* g) {
     // FFT: attraction, grid + bin + scan + scatter, spread, rows, cols, rows, gather +
     // update; two more spectrum kernels for the shared-memory FFT (P = 8192)
     if (g->params.rep_mode == TFDP_REP_EXACT) return 2;
-    return (1 + 4 + 1 + 1 + 1 + 1 + 1) + (g->logP > 12 ? 2 : 0);
+    const int k = g->k_now();
+    const int lp = (k >= 1 && k <= kMaxK && g->logP_k[k]) ? g->logP_k[k] : g->logP;
+    return (1 + 4 + 1 + 1 + 1 + 1 + 1) + (lp > 12 ? 2 : 0);
 }
 
 long long exec_key_of(const tfdp_graph* g, int k) {
@@ -663,7 +712,8 @@ tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
         if (!fft_geometry(*p, &P, &l, &G, &nb)) return TFDP_ERR_PARAM_RANGE;
         if ((nb + scan_items_per_block() - 1) / scan_items_per_block() > 1024) return TFDP_ERR_PARAM_RANGE;
         // the tensor-core column stage is built for the 64 x 32 factorisation of P = 2048
-        if (p->precision == TFDP_PREC_BF16X3 && P != 2048) return TFDP_ERR_PARAM_RANGE;
+        if (p->precision == TFDP_PREC_BF16X3 && (P != 2048 || p->k_interp == TFDP_K_DYNAMIC))
+            return TFDP_ERR_PARAM_RANGE;
     }
     if (weight_ok) *weight_ok = (p->alpha * (1.0 + p->beta) < 1.0) ? 1 : 0;
     return TFDP_OK;
@@ -942,7 +992,8 @@ tfdp_status tfdp_get_stats(tfdp_graph* g, tfdp_stats* out) {
     out->grid_h = s.grid.h;
     out->grid_n_int = s.grid.n_int;
     out->grid_G = s.grid.G;
-    out->fft_P = g->P;
+    // the FFT size of the order k of the last iteration or force evaluation
+    out->fft_P = (s.grid.k >= 1 && s.grid.k <= kMaxK && g->logP_k[s.grid.k]) ? (1 << g->logP_k[s.grid.k]) : g->P;
     out->spectrum_builds = s.spec_builds;
     out->device_flags = (int32_t)(s.flags | g->flags_seen);
     out->kernels_per_iteration = kernels_per_iteration(g);
@@ -1084,6 +1135,9 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
         b += nn * (sizeof(int2) + 2 * sizeof(int) + 2 * sizeof(float2));
         b += sizeof(float) * 3 * Gs * Gs + 2 * sizeof(float2) * 3 * NH * ys + sizeof(float4) * Gs * Gs;
         b += sizeof(float2) * 3 * NH * P + 3 * sizeof(float) * NH * P + sizeof(float2) * P + 32 * 256;
+        b += 3 * sizeof(float2) * P + 3 * 256;  // per-k twiddle tables (each at most P entries)
+        if (p.precision == TFDP_PREC_BF16X3)
+            b += tc_constants_bytes() + sizeof(float) * tc_spectrum_floats() + 2 * 256;
     }
     *bytes = b;
     return TFDP_OK;
