@@ -259,11 +259,12 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
 tfdp_status tfdp_destroy_graph(tfdp_graph* g);
 
 /*
- * Batches: many independent graphs advanced together by one cooperative persistent
- * kernel per call (Sec. 3.4 ibFFT path for every graph; the batching itself has no
- * counterpart in the paper). Graphs keep their own parameters, grids, spectra, state
- * and iteration counters; the arithmetic per graph is that of a single graph, so each
- * graph's result equals its solo run up to floating-point summation order.
+ * Batches: many independent graphs advanced together by cooperative persistent kernels
+ * (Sec. 3.4 ibFFT path for every graph; the batching itself has no counterpart in the
+ * paper). Graphs keep their own parameters, grids, spectra, state and iteration
+ * counters; the arithmetic per graph is that of a single graph, so each graph's result
+ * equals its solo run. Graphs are grouped into parts by (k_interp, FFT size); each call
+ * runs one persistent launch per part, the parts one after another on the stream.
  */
 typedef struct tfdp_batch tfdp_batch;
 
@@ -273,10 +274,10 @@ typedef struct tfdp_batch tfdp_batch;
  *   edges      per graph host pointer to 2 m int32 ids (NULL allowed when m = 0)
  *   xy0        per graph host pointer to n x 2 FP32 initial positions
  *   params     NULL (defaults for all) or num_graphs parameter sets; rep_mode is forced
- *              to TFDP_REP_FFT; all graphs must share one fixed k_interp (1..3;
- *              TFDP_K_DYNAMIC gives TFDP_ERR_PARAM_RANGE). The FFT size is the
- *              largest any graph needs and must be <= 2048 (grid_max <= 1024), else
- *              TFDP_ERR_PARAM_RANGE.
+ *              to TFDP_REP_FFT; each graph has a fixed k_interp (1..3; TFDP_K_DYNAMIC
+ *              gives TFDP_ERR_PARAM_RANGE) and FP32 precision; a graph's FFT size
+ *              follows from its grid_max and k and must be <= 2048 (grid_max <= 1024),
+ *              else TFDP_ERR_PARAM_RANGE. Graphs of the same (k, FFT size) share a part.
  *   stream     cudaStream_t for all work of the batch
  * Inputs are copied. Errors as for tfdp_create_graph.
  */
@@ -302,8 +303,36 @@ tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out);
 tfdp_status tfdp_batch_synchronize(tfdp_batch* b);
 tfdp_status tfdp_batch_destroy(tfdp_batch* b);
 
-/* CTAs of the cooperative launch (all co-resident on the device), 0 for NULL. */
+/* CTAs of the cooperative launch of the largest part (all co-resident on the device),
+ * 0 for NULL. */
 int32_t tfdp_batch_grid_blocks(const tfdp_batch* b);
+
+/* Number of parts (distinct (k_interp, FFT size) groups) of the batch, 0 for NULL. */
+int32_t tfdp_batch_num_parts(const tfdp_batch* b);
+
+/*
+ * Grid autotuner for batches (points per cell and grid size of Sec. 3.4, per graph; the
+ * tuning itself has no counterpart in the paper). For every graph it picks the
+ * interpolation order k and the grid cap with the cheapest FFT (size first, then k) whose
+ * repulsion error against the exact all-pairs sum of the same positions is at most
+ * max(max_error_ratio x the error of the reference parameters `base` (NULL: defaults),
+ * min_error_bound), measured on the GPU with the single-graph API (one exact and a few
+ * FFT force evaluations per measured graph, O(n^2) for the exact one). The candidates are
+ * every k = 1..3 at each FFT size below the reference's (grid cap P / 2), then the
+ * reference itself. Graphs are grouped by size (half octaves of n); up to `probes` graphs
+ * of each group are measured and the group takes the cheapest candidate that meets the
+ * bound on every measured graph.
+ *   out_params  num_graphs sets: `base` with k_interp and grid_max chosen per graph
+ *   out_error   NULL or num_graphs values: the largest measured error of the chosen
+ *               setting in the graph's group
+ * Synchronises the current device's work it launches; allocates and frees temporary
+ * graphs. TFDP_ERR_INVALID_ARG for bad pointers, probes < 1, max_error_ratio < 1 or
+ * min_error_bound < 0.
+ */
+tfdp_status tfdp_batch_plan(int32_t num_graphs, const int64_t* n, const int64_t* m, const int32_t* const* edges,
+                            const float* const* xy0, const tfdp_params* base, double max_error_ratio,
+                            double min_error_bound, int32_t probes, tfdp_params* out_params,
+                            double* out_error);
 
 /* Launch-shape autotuner: times `trials` force evaluations of the whole batch for each
  * number of co-resident CTAs per SM the kernel allows and keeps the fastest

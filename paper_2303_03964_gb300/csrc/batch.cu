@@ -1,7 +1,7 @@
 // batch.cu -- many graphs advanced together by one cooperative persistent kernel.
 //
 // A batch holds B independent graphs in packed arenas (positions, CSR, sort buffers)
-// with per-graph parameters, state, grids and spectra. tfdp_batch_iterate runs `iters`
+// with per-graph parameters, state, grids and spectra. An iteration call runs `iters`
 // t-FDP iterations of every graph in a single launch: the kernel walks through the
 // nine phases of an iteration (grid policy; binning + attraction; per-graph scan;
 // scatter; spread; row / column / inverse-row FFT stages; back-projection + update),
@@ -9,9 +9,11 @@
 // between phases. The per-node and per-transform arithmetic is the single-graph code
 // (node_dev.cuh, fft_stages.cuh), so every graph evolves as it would alone.
 //
-// All graphs of a batch share k and the FFT size P (the largest any graph needs:
-// P >= 2 G_max - 1 for every graph, so each graph's linear convolution is exact). The
-// kernel itself is in batch_kernel.cuh.
+// A batch is split into parts by (k, FFT size): each part is one such persistent launch
+// whose graphs share k and P (P >= 2 G_max - 1 for every graph of the part, so each
+// graph's linear convolution is exact), and the parts run one after another on the
+// batch's stream. tfdp_batch_plan picks k and the grid cap per graph by measurement, so
+// that small graphs run on smaller transforms. The kernel itself is in batch_kernel.cuh.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -86,7 +88,7 @@ int log2c(long long v) {
 
 }  // namespace
 
-struct tfdp_batch {
+struct BatchPart {
     int B = 0;
     int64_t N = 0, M = 0;
     int k = 3, logP = 9, P = 512;
@@ -115,8 +117,8 @@ namespace {
 // Wait for the batch's stream and report the device flags that graphs [g0, g1) raised
 // since the last report (TFDP_ERR_TIMEOUT for a wait that gave up, else
 // TFDP_ERR_DEVICE_CHECK); the flags are then cleared on the device and kept per graph
-// for tfdp_batch_get_stats.
-tfdp_status batch_sync_checked(tfdp_batch* b, int g0, int g1) {
+// for the stats call.
+tfdp_status batch_sync_checked(BatchPart* b, int g0, int g1) {
     const int cnt = g1 - g0;
     if (cnt > 0) {
         BK(cudaMemcpy2DAsync(b->flags_word.data() + g0, sizeof(unsigned), &b->d_st[g0].flags, sizeof(DevState),
@@ -136,7 +138,7 @@ tfdp_status batch_sync_checked(tfdp_batch* b, int g0, int g1) {
     return (all & FLAG_WAIT_TIMEOUT) ? TFDP_ERR_TIMEOUT : TFDP_ERR_DEVICE_CHECK;
 }
 
-cudaError_t batch_launch(const tfdp_batch* b, const BatchArgs& a, cudaStream_t s) {
+cudaError_t batch_launch(const BatchPart* b, const BatchArgs& a, cudaStream_t s) {
     switch (b->k) {
         case 1: return batch_launch_k<1>(b->logP, a, b->grid_blocks, s);
         case 2: return batch_launch_k<2>(b->logP, a, b->grid_blocks, s);
@@ -144,7 +146,7 @@ cudaError_t batch_launch(const tfdp_batch* b, const BatchArgs& a, cudaStream_t s
         default: return cudaErrorInvalidValue;
     }
 }
-cudaError_t batch_occupancy(const tfdp_batch* b, int* bps) {
+cudaError_t batch_occupancy(const BatchPart* b, int* bps) {
     switch (b->k) {
         case 1: return batch_occupancy_k<1>(b->logP, bps);
         case 2: return batch_occupancy_k<2>(b->logP, bps);
@@ -153,7 +155,7 @@ cudaError_t batch_occupancy(const tfdp_batch* b, int* bps) {
     }
 }
 
-tfdp_status upload_batch_params(tfdp_batch* b) {
+tfdp_status upload_batch_params(BatchPart* b) {
     std::vector<DevParams> dp((size_t)b->B);
     std::vector<double> steps((size_t)b->B * b->T_max, 0.0);
     for (int g = 0; g < b->B; ++g) {
@@ -186,7 +188,7 @@ tfdp_status upload_batch_params(tfdp_batch* b) {
     return TFDP_OK;
 }
 
-tfdp_status batch_refresh(tfdp_batch* b) {
+tfdp_status batch_refresh(BatchPart* b) {
     const int slot = (int)(b->host_iter & 1);
     for (int g = 0; g < b->B; ++g) {
         const unsigned init[2] = {kOrdMinInit, kOrdMaxInit};
@@ -205,12 +207,14 @@ tfdp_status batch_refresh(tfdp_batch* b) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_t* m, const int32_t* const* edges,
-                              const float* const* xy0, const tfdp_params* params, void* stream, tfdp_batch** out) {
+tfdp_status part_destroy(BatchPart* b);
+
+tfdp_status part_create(int32_t num_graphs, const int64_t* n, const int64_t* m, const int32_t* const* edges,
+                              const float* const* xy0, const tfdp_params* params, void* stream, BatchPart** out) {
     if (!out || num_graphs < 1 || !n || !m || !edges || !xy0) return TFDP_ERR_INVALID_ARG;
-    tfdp_batch* b = new (std::nothrow) tfdp_batch();
+    BatchPart* b = new (std::nothrow) BatchPart();
     if (!b) return TFDP_ERR_OUT_OF_MEMORY;
     b->B = num_graphs;
     b->stream = (cudaStream_t)stream;
@@ -395,7 +399,7 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
         G.specHy = (float*)sub(sizeof(float) * NH * b->P);
     }
     auto fail = [&](tfdp_status s) {
-        tfdp_batch_destroy(b);
+        part_destroy(b);
         return s;
     };
     std::vector<float2> tw((size_t)b->P);
@@ -435,7 +439,7 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
     return TFDP_OK;
 }
 
-tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters) {
+tfdp_status part_iterate(BatchPart* b, int32_t iters) {
     if (!b || iters < 0) return TFDP_ERR_INVALID_ARG;
     if (iters == 0) return TFDP_OK;
     if (b->no_graph) {  // the cooperative launch could not be captured: launch directly
@@ -467,7 +471,7 @@ tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters) {
         if (e != cudaSuccess) {
             cudaGetLastError();  // clear the capture error, fall back to direct launches
             b->no_graph = true;
-            return tfdp_batch_iterate(b, iters);
+            return part_iterate(b, iters);
         }
         b->exec_iters = iters;
     }
@@ -476,7 +480,7 @@ tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters) {
     return TFDP_OK;
 }
 
-tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, float* fatt, int on_device) {
+tfdp_status part_eval_forces(BatchPart* b, int32_t graph, float* frep, float* fatt, int on_device) {
     if (!b || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
     BatchArgs a = b->args;
     a.iters = 1;
@@ -490,7 +494,7 @@ tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, fl
     return batch_sync_checked(b, graph, graph + 1);
 }
 
-tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, int on_device) {
+tfdp_status part_get_positions(BatchPart* b, int32_t graph, float* xy, int on_device) {
     if (!b || !xy || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
     const int slot = (int)(b->host_iter & 1);
     BK(cudaMemcpyAsync(xy, b->args.xy[slot] + b->node_off[(size_t)graph], sizeof(float2) * (size_t)b->n[(size_t)graph],
@@ -498,7 +502,7 @@ tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, in
     return batch_sync_checked(b, graph, graph + 1);
 }
 
-tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) {
+tfdp_status part_get_stats(BatchPart* b, int32_t graph, tfdp_stats* out) {
     if (!b || !out || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
     DevState s;
     BK(cudaMemcpyAsync(&s, b->d_st + graph, sizeof(DevState), cudaMemcpyDeviceToHost, b->stream));
@@ -518,12 +522,12 @@ tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) 
     return TFDP_OK;
 }
 
-tfdp_status tfdp_batch_synchronize(tfdp_batch* b) {
+tfdp_status part_synchronize(BatchPart* b) {
     if (!b) return TFDP_ERR_INVALID_ARG;
     return batch_sync_checked(b, 0, b->B);
 }
 
-tfdp_status tfdp_batch_destroy(tfdp_batch* b) {
+tfdp_status part_destroy(BatchPart* b) {
     if (!b) return TFDP_OK;
     if (b->mem) cudaStreamSynchronize(b->stream);
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -532,9 +536,9 @@ tfdp_status tfdp_batch_destroy(tfdp_batch* b) {
     return TFDP_OK;
 }
 
-int32_t tfdp_batch_grid_blocks(const tfdp_batch* b) { return b ? b->grid_blocks : 0; }
+int32_t part_grid_blocks(const BatchPart* b) { return b ? b->grid_blocks : 0; }
 
-tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_blocks) {
+tfdp_status part_autotune(BatchPart* b, int32_t trials, int32_t* chosen_blocks) {
     if (!b || trials < 1) return TFDP_ERR_INVALID_ARG;
     int bps = 0, sms = 0, dev = 0;
     BK(batch_occupancy(b, &bps));
@@ -575,4 +579,279 @@ tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_b
     return TFDP_OK;
 }
 
+}  // namespace
+
+// ------------------------------------------------------------------ batches of parts
+struct tfdp_batch {
+    int B = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<BatchPart*> parts;
+    std::vector<int> part_of, local_of;  // graph -> (part, index in the part)
+};
+
+namespace {
+
+int batch_log2p(const tfdp_params& p) {
+    const int G = (p.grid_max / p.k_interp) * p.k_interp;
+    return std::max(7, log2c(2LL * G - 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_t* m, const int32_t* const* edges,
+                              const float* const* xy0, const tfdp_params* params, void* stream, tfdp_batch** out) {
+    if (!out || num_graphs < 1 || !n || !m || !edges || !xy0) return TFDP_ERR_INVALID_ARG;
+    // parts: graphs grouped by (k, FFT size), in order of first appearance
+    std::vector<std::pair<int, int>> keys;
+    std::vector<int> part_of((size_t)num_graphs), local_of((size_t)num_graphs);
+    std::vector<std::vector<int>> members;
+    for (int g = 0; g < num_graphs; ++g) {
+        tfdp_params p;
+        if (params) p = params[g];
+        else tfdp_params_default(&p);
+        p.rep_mode = TFDP_REP_FFT;
+        tfdp_status st = tfdp_params_check(&p, nullptr);
+        if (st != TFDP_OK) return st;
+        if (p.k_interp == TFDP_K_DYNAMIC) return TFDP_ERR_PARAM_RANGE;  // one fixed k per graph
+        const std::pair<int, int> key(p.k_interp, batch_log2p(p));
+        size_t q = 0;
+        while (q < keys.size() && keys[q] != key) ++q;
+        if (q == keys.size()) {
+            keys.push_back(key);
+            members.emplace_back();
+        }
+        part_of[(size_t)g] = (int)q;
+        local_of[(size_t)g] = (int)members[q].size();
+        members[q].push_back(g);
+    }
+    tfdp_batch* b = new (std::nothrow) tfdp_batch();
+    if (!b) return TFDP_ERR_OUT_OF_MEMORY;
+    b->B = num_graphs;
+    b->stream = (cudaStream_t)stream;
+    b->part_of = part_of;
+    b->local_of = local_of;
+    for (size_t q = 0; q < members.size(); ++q) {
+        const size_t c = members[q].size();
+        std::vector<int64_t> pn(c), pm(c);
+        std::vector<const int32_t*> pe(c);
+        std::vector<const float*> px(c);
+        std::vector<tfdp_params> pp(c);
+        for (size_t i = 0; i < c; ++i) {
+            const int g = members[q][i];
+            pn[i] = n[g];
+            pm[i] = m[g];
+            pe[i] = edges[g];
+            px[i] = xy0[g];
+            if (params) pp[i] = params[g];
+            else tfdp_params_default(&pp[i]);
+        }
+        BatchPart* part = nullptr;
+        const tfdp_status st = part_create((int32_t)c, pn.data(), pm.data(), pe.data(), px.data(), pp.data(), stream,
+                                           &part);
+        if (st != TFDP_OK) {
+            tfdp_batch_destroy(b);
+            return st;
+        }
+        b->parts.push_back(part);
+    }
+    *out = b;
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters) {
+    if (!b || iters < 0) return TFDP_ERR_INVALID_ARG;
+    for (BatchPart* part : b->parts) {
+        const tfdp_status st = part_iterate(part, iters);
+        if (st != TFDP_OK) return st;
+    }
+    return TFDP_OK;
+}
+
+tfdp_status tfdp_batch_eval_forces(tfdp_batch* b, int32_t graph, float* frep, float* fatt, int on_device) {
+    if (!b || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    return part_eval_forces(b->parts[(size_t)b->part_of[(size_t)graph]], b->local_of[(size_t)graph], frep, fatt,
+                            on_device);
+}
+
+tfdp_status tfdp_batch_get_positions(tfdp_batch* b, int32_t graph, float* xy, int on_device) {
+    if (!b || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    return part_get_positions(b->parts[(size_t)b->part_of[(size_t)graph]], b->local_of[(size_t)graph], xy,
+                              on_device);
+}
+
+tfdp_status tfdp_batch_get_stats(tfdp_batch* b, int32_t graph, tfdp_stats* out) {
+    if (!b || graph < 0 || graph >= b->B) return TFDP_ERR_INVALID_ARG;
+    return part_get_stats(b->parts[(size_t)b->part_of[(size_t)graph]], b->local_of[(size_t)graph], out);
+}
+
+tfdp_status tfdp_batch_synchronize(tfdp_batch* b) {
+    if (!b) return TFDP_ERR_INVALID_ARG;
+    tfdp_status first = TFDP_OK;
+    for (BatchPart* part : b->parts) {
+        const tfdp_status st = part_synchronize(part);
+        if (first == TFDP_OK) first = st;
+    }
+    return first;
+}
+
+tfdp_status tfdp_batch_destroy(tfdp_batch* b) {
+    if (!b) return TFDP_OK;
+    for (BatchPart* part : b->parts) part_destroy(part);
+    delete b;
+    return TFDP_OK;
+}
+
+int32_t tfdp_batch_grid_blocks(const tfdp_batch* b) {
+    int32_t best = 0;
+    if (b)
+        for (const BatchPart* part : b->parts) best = std::max(best, part_grid_blocks(part));
+    return best;
+}
+
+tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_blocks) {
+    if (!b || trials < 1) return TFDP_ERR_INVALID_ARG;
+    int32_t best = 0;
+    for (BatchPart* part : b->parts) {
+        int32_t c = 0;
+        const tfdp_status st = part_autotune(part, trials, &c);
+        if (st != TFDP_OK) return st;
+        best = std::max(best, c);
+    }
+    if (chosen_blocks) *chosen_blocks = best;
+    return TFDP_OK;
+}
+
+int32_t tfdp_batch_num_parts(const tfdp_batch* b) { return b ? (int32_t)b->parts.size() : 0; }
+
 }  // extern "C"
+
+namespace {
+
+// Relative L2 distance of two n x 2 force fields.
+double rel_l2(const std::vector<float>& a, const std::vector<float>& ref) {
+    double num = 0.0, den = 0.0;
+    for (size_t i = 0; i < ref.size(); ++i) {
+        const double d = (double)a[i] - (double)ref[i];
+        num += d * d;
+        den += (double)ref[i] * (double)ref[i];
+    }
+    return den > 0.0 ? std::sqrt(num / den) : std::sqrt(num);
+}
+
+// Force error of the ibFFT at each candidate (k, grid cap) and at the reference
+// parameters, against the exact sum of the same positions, for one graph (GPU).
+tfdp_status probe_errors(int64_t n, int64_t m, const int32_t* edges, const float* xy, const tfdp_params& base,
+                         const std::vector<std::pair<int, int>>& cand, double* err_ref, std::vector<double>& err) {
+    tfdp_params p = base;
+    p.rep_mode = TFDP_REP_EXACT;
+    tfdp_graph* g = nullptr;
+    tfdp_status st = tfdp_create_graph(n, m, edges, xy, 0, &p, nullptr, &g);
+    if (st != TFDP_OK) return st;
+    std::vector<float> exact((size_t)(2 * n)), f((size_t)(2 * n));
+    st = tfdp_eval_forces(g, exact.data(), nullptr, 0);
+    p.rep_mode = TFDP_REP_FFT;
+    if (st == TFDP_OK) st = tfdp_set_params(g, &p);
+    if (st == TFDP_OK) st = tfdp_eval_forces(g, f.data(), nullptr, 0);
+    if (st == TFDP_OK) *err_ref = rel_l2(f, exact);
+    err.assign(cand.size(), 1e300);
+    for (size_t c = 0; c < cand.size() && st == TFDP_OK; ++c) {
+        tfdp_params q = p;
+        q.k_interp = cand[c].first;
+        q.grid_max = cand[c].second;
+        st = tfdp_set_params(g, &q);
+        if (st == TFDP_OK) st = tfdp_eval_forces(g, f.data(), nullptr, 0);
+        if (st == TFDP_OK) err[c] = rel_l2(f, exact);
+    }
+    tfdp_destroy_graph(g);
+    return st;
+}
+
+}  // namespace
+
+extern "C" tfdp_status tfdp_batch_plan(int32_t num_graphs, const int64_t* n, const int64_t* m,
+                                       const int32_t* const* edges, const float* const* xy0,
+                                       const tfdp_params* base, double max_error_ratio, double min_error_bound,
+                                       int32_t probes, tfdp_params* out_params, double* out_error) {
+    if (num_graphs < 1 || !n || !m || !edges || !xy0 || !out_params || probes < 1 || !(max_error_ratio >= 1.0) ||
+        !(min_error_bound >= 0.0))
+        return TFDP_ERR_INVALID_ARG;
+    tfdp_params ref;
+    if (base) ref = *base;
+    else tfdp_params_default(&ref);
+    ref.rep_mode = TFDP_REP_FFT;
+    tfdp_status st = tfdp_params_check(&ref, nullptr);
+    if (st != TFDP_OK) return st;
+    if (ref.k_interp == TFDP_K_DYNAMIC || ref.precision != TFDP_PREC_FP32) return TFDP_ERR_PARAM_RANGE;
+    for (int g = 0; g < num_graphs; ++g)
+        if (n[g] < 1 || m[g] < 0 || (m[g] > 0 && !edges[g]) || !xy0[g]) return TFDP_ERR_INVALID_ARG;
+    // candidates in order of cost: smaller FFT sizes than the reference's (the transforms
+    // dominate small graphs), each with k = 1..3 (k^2 grid nodes per node in the spread
+    // and gather), then the reference itself; at the reference's FFT size another k would
+    // only split the batch into more launches for little saving
+    const int ref_log = batch_log2p(ref);
+    std::vector<std::pair<int, int>> cand;
+    for (int lp = 7; lp < ref_log; ++lp) {
+        const int gm = std::min(1 << (lp - 1), ref.grid_max);  // G <= P / 2 keeps 2 G - 1 <= P
+        for (int k = 1; k <= kMaxK; ++k) {
+            if (gm / k < 1) continue;
+            tfdp_params q = ref;
+            q.k_interp = k;
+            q.grid_max = gm;
+            if (tfdp_params_check(&q, nullptr) != TFDP_OK || batch_log2p(q) != lp) continue;
+            cand.emplace_back(k, gm);
+        }
+    }
+    cand.emplace_back(ref.k_interp, ref.grid_max);
+    // groups: half octaves of n
+    std::vector<int> group((size_t)num_graphs);
+    int ngroups = 0;
+    for (int g = 0; g < num_graphs; ++g) {
+        group[(size_t)g] = (int)std::floor(2.0 * std::log2((double)n[g]));
+        ngroups = std::max(ngroups, group[(size_t)g] + 1);
+    }
+    std::vector<int> choice((size_t)ngroups, -1), probed((size_t)ngroups, 0);
+    std::vector<double> worst((size_t)ngroups, 0.0);
+    std::vector<std::vector<char>> ok((size_t)ngroups, std::vector<char>(cand.size(), 1));
+    std::vector<double> worst_c((size_t)ngroups * cand.size(), 0.0);
+    std::vector<double> errs;
+    double e_ref = 0.0;
+    for (int g = 0; g < num_graphs; ++g) {
+        const int q = group[(size_t)g];
+        if (probed[(size_t)q] >= probes) continue;
+        st = probe_errors(n[g], m[g], edges[g], xy0[g], ref, cand, &e_ref, errs);
+        if (st != TFDP_OK) return st;
+        ++probed[(size_t)q];
+        for (size_t c = 0; c < cand.size(); ++c) {
+            if (!(errs[c] <= std::max(max_error_ratio * e_ref, min_error_bound))) ok[(size_t)q][c] = 0;
+            worst_c[(size_t)q * cand.size() + c] = std::max(worst_c[(size_t)q * cand.size() + c], errs[c]);
+        }
+        worst[(size_t)q] = std::max(worst[(size_t)q], e_ref);
+    }
+    for (int q = 0; q < ngroups; ++q) {
+        if (!probed[(size_t)q]) continue;
+        for (size_t c = 0; c < cand.size(); ++c)
+            if (ok[(size_t)q][c]) {
+                choice[(size_t)q] = (int)c;
+                break;
+            }
+    }
+    for (int g = 0; g < num_graphs; ++g) {
+        const int q = group[(size_t)g];
+        tfdp_params p = base ? base[0] : ref;
+        p.rep_mode = TFDP_REP_FFT;
+        double e = worst[(size_t)q];
+        if (choice[(size_t)q] >= 0) {
+            p.k_interp = cand[(size_t)choice[(size_t)q]].first;
+            p.grid_max = cand[(size_t)choice[(size_t)q]].second;
+            e = worst_c[(size_t)q * cand.size() + (size_t)choice[(size_t)q]];
+        } else {
+            p.k_interp = ref.k_interp;
+            p.grid_max = ref.grid_max;
+        }
+        out_params[g] = p;
+        if (out_error) out_error[g] = e;
+    }
+    return TFDP_OK;
+}

@@ -95,6 +95,7 @@ struct tfdp_graph {
 
     // FFT arena
     void* fft_mem = nullptr;
+    unsigned fft_gen = 0;             // FFT arenas allocated so far (a new one may reuse the old address)
     int fft_k = 0, fft_grid_max = 0;  // what the FFT arena was sized for
     int P = 0, logP = 0, G_max = 0, Gs = 0, ystride = 0, nbox_max = 0;
     int* cnt = nullptr;
@@ -359,6 +360,7 @@ tfdp_status alloc_fft(tfdp_graph* g) {
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fft arena)");
     char* b = (char*)mem;
     g->fft_mem = mem;
+    ++g->fft_gen;
     g->order_valid[0] = g->order_valid[1] = false;  // the visit orders of a new arena are unset
     g->cnt = (int*)(b + o_cnt);
     g->off = (int*)(b + o_off);
@@ -863,10 +865,11 @@ tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
     if (prec_changed && g->dst)  // each precision mode keeps its own spectrum arrays
         CK(cudaMemsetAsync(&g->dst->spec_valid, 0, sizeof(int), g->stream));
     if (p->rep_mode == TFDP_REP_FFT) {
-        void* before = g->fft_mem;
+        // compare generations, not addresses: a new arena can land where the old one was
+        const unsigned before = g->fft_gen;
         st = alloc_fft(g);
         if (st != TFDP_OK) return st;
-        if ((to_fft || g->fft_mem != before) && g->n > 0) {
+        if ((to_fft || g->fft_gen != before) && g->n > 0) {
             CK(launch_order_reset(g->node_launch(), (int)(g->host_iter & 1), g->stream));
             g->order_valid[g->host_iter & 1] = true;
         }

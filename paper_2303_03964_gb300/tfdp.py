@@ -97,6 +97,9 @@ _SIGS = {
     "tfdp_batch_destroy": ([_p], ctypes.c_int),
     "tfdp_batch_grid_blocks": ([_p], ctypes.c_int32),
     "tfdp_batch_autotune": ([_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "tfdp_batch_num_parts": ([_p], ctypes.c_int32),
+    "tfdp_batch_plan": ([ctypes.c_int32, _p, _p, _p, _p, _p, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
+                         _p, _p], ctypes.c_int),
     "tfdp_graph_set_stream": ([_p, _p], ctypes.c_int),
     "tfdp_graph_footprint": ([ctypes.c_int64, ctypes.c_int64, _p, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "tfdp_server_create": ([ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_p)], ctypes.c_int),
@@ -364,22 +367,52 @@ def exact_repulsion_noalloc(xy, frep, gamma=2.0, stream=0):
     return frep
 
 
+def _graph_arrays(graphs):
+    """Per-graph host arrays and pointer tables of a list of (n, edges, xy0)."""
+    B = len(graphs)
+    n = np.array([int(g[0]) for g in graphs], dtype=np.int64)
+    edges = [np.ascontiguousarray(np.asarray(g[1], dtype=np.int32).reshape(-1, 2)) for g in graphs]
+    xy = [_host_f32(g[2], int(g[0])) for g in graphs]
+    m = np.array([e.shape[0] for e in edges], dtype=np.int64)
+    eptr = (_p * B)(*[e.ctypes.data if e.shape[0] else None for e in edges])
+    xptr = (_p * B)(*[x.ctypes.data for x in xy])
+    return n, m, edges, xy, eptr, xptr
+
+
+def batch_plan(graphs, base=None, max_error_ratio=1.5, min_error_bound=0.0, probes=2):
+    """Grid autotuner (tfdp_batch_plan): per graph, the k_interp and grid cap with the
+    cheapest FFT whose measured repulsion error is within max(max_error_ratio x the error
+    of ``base`` (None: defaults), min_error_bound). Returns (list of Params, numpy array
+    of errors)."""
+    B = len(graphs)
+    n, m, edges, xy, eptr, xptr = _graph_arrays(graphs)
+    out = (Params * B)()
+    err = np.zeros(B, dtype=np.float64)
+    _check(lib.tfdp_batch_plan(B, n.ctypes.data_as(_p), m.ctypes.data_as(_p), ctypes.cast(eptr, _p),
+                               ctypes.cast(xptr, _p), ctypes.byref(base) if base is not None else None,
+                               float(max_error_ratio), float(min_error_bound), int(probes), ctypes.cast(out, _p),
+                               err.ctypes.data_as(_p)),
+           "tfdp_batch_plan")
+    params = []
+    for i in range(B):
+        p = Params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(out[i]), ctypes.sizeof(Params))
+        params.append(p)
+    return params, err
+
+
 class Batch:
-    """Many graphs advanced together by one persistent launch (wraps tfdp_batch).
+    """Many graphs advanced together by persistent launches (wraps tfdp_batch).
 
     ``graphs`` is a list of (n, edges (m x 2 int32), xy0 (n x 2 float32)); ``params`` is
-    None (defaults) or one Params per graph (all with the same k_interp).
+    None (defaults) or one Params per graph; graphs with the same (k_interp, FFT size)
+    share one persistent launch (a part).
     """
 
     def __init__(self, graphs, params=None, stream=0):
         B = len(graphs)
         self.B = B
-        self._n = np.array([int(g[0]) for g in graphs], dtype=np.int64)
-        self._edges = [np.ascontiguousarray(np.asarray(g[1], dtype=np.int32).reshape(-1, 2)) for g in graphs]
-        self._xy = [_host_f32(g[2], int(g[0])) for g in graphs]
-        m = np.array([e.shape[0] for e in self._edges], dtype=np.int64)
-        eptr = (_p * B)(*[e.ctypes.data if e.shape[0] else None for e in self._edges])
-        xptr = (_p * B)(*[x.ctypes.data for x in self._xy])
+        self._n, m, self._edges, self._xy, eptr, xptr = _graph_arrays(graphs)
         prm = None
         if params is not None:
             prm = (Params * B)()
@@ -435,6 +468,9 @@ class Batch:
 
     def grid_blocks(self):
         return int(lib.tfdp_batch_grid_blocks(self._h))
+
+    def num_parts(self):
+        return int(lib.tfdp_batch_num_parts(self._h))
 
     def autotune(self, trials=3):
         c = ctypes.c_int32(0)

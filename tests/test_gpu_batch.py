@@ -81,10 +81,65 @@ def test_batch_layout_equals_solo(tfdp):
             assert _rel(out_b, out_s) <= POS_TOL, (q, _rel(out_b, out_s))
 
 
-def test_batch_rejects_mixed_k_and_bad_graph(tfdp):
+def test_batch_parts_of_mixed_k_and_fft_size_equal_solo(tfdp):
+    """Graphs with different k and grid caps run as several parts (one persistent launch
+    per (k, FFT size)); each graph still gives its solo run's forces and layout, and the
+    oracle's ibFFT at its own grid."""
+    graphs = _mixed_graphs(8, 91, nmin=400, nmax=5000)
+    settings = [(1, 63), (2, 127), (3, 255), (1, 255), (3, 127), (2, 63), (1, 127), (3, 255)]
+    params = [tfdp.params_default(k_interp=k, grid_max=gm, total_iters=40) for k, gm in settings]
+    with tfdp.Batch(graphs, params) as b:
+        assert b.num_parts() == len(set((k, max(7, int(np.ceil(np.log2(2 * (gm // k) * k - 1)))))
+                                        for k, gm in settings))
+        for q, (n, e, xy) in enumerate(graphs):
+            fr_b, _ = b.eval_forces(q)
+            with tfdp.Graph(n, e, xy, params[q]) as g:
+                fr_s, _ = g.eval_forces()
+                st = g.stats()
+            assert _rel(fr_b, fr_s) <= FORCE_TOL, (q, _rel(fr_b, fr_s))
+            assert b.stats(q)["fft_P"] == st["fft_P"] and b.stats(q)["grid_G"] == st["grid_G"]
+            k, gm = settings[q]
+            grid = oracle.grid_policy(xy, k, 50, gm)
+            ref = oracle.rep_fft(xy.astype(np.float64), 2.0, k, grid=grid, xy_f32=xy)
+            assert _rel(fr_b, ref) <= FORCE_TOL, (q, _rel(fr_b, ref))
+        b.iterate(6)
+        for q, (n, e, xy) in enumerate(graphs):
+            with tfdp.Graph(n, e, xy, params[q]) as g:
+                g.iterate(6)
+                assert _rel(b.get_positions(q), g.get_positions()) <= POS_TOL
+
+
+def test_batch_plan_meets_its_error_bound(tfdp):
+    """The grid autotuner's choice per graph: an FFT no larger than the reference's, and a
+    repulsion error against the exact sum within the requested ratio of the reference
+    parameters' error (checked here on every graph, also the ones it did not measure)."""
+    graphs = _mixed_graphs(12, 93, nmin=800, nmax=20000)
+    base = tfdp.params_default(grid_max=255)
+    ratio, floor = 1.5, 0.02
+    params, err = tfdp.batch_plan(graphs, base, max_error_ratio=ratio, min_error_bound=floor, probes=2)
+    assert len(params) == len(graphs) and np.all(np.isfinite(err))
+    sizes = []
+    for q, (n, e, xy) in enumerate(graphs):
+        p = params[q]
+        assert p.gamma == base.gamma and p.rep_mode == tfdp.REP_FFT and 1 <= p.k_interp <= 3
+        with tfdp.Graph(n, e, xy, p) as g:
+            fr, _ = g.eval_forces()
+            sizes.append(g.stats()["fft_P"])
+        with tfdp.Graph(n, e, xy, base) as g:
+            fr_ref, _ = g.eval_forces()
+            assert sizes[-1] <= g.stats()["fft_P"]
+        rows = np.random.default_rng(q).choice(n, min(n, 1000), replace=False)
+        ex = oracle.rep_exact(xy.astype(np.float64), 2.0, rows=rows)
+        e_ref, e_got = _rel(fr_ref[rows], ex), _rel(fr[rows], ex)
+        # graphs the tuner did not measure share their size group's choice: allow a margin
+        assert e_got <= 1.25 * max(ratio * e_ref, floor) + 1e-4, (q, n, e_got, e_ref)
+    with tfdp.Batch(graphs, params) as b:
+        b.iterate(2)
+        b.synchronize()
+
+
+def test_batch_rejects_dynamic_k_and_bad_graph(tfdp):
     g1 = (10, [[0, 1]], np.zeros((10, 2), np.float32))
-    with pytest.raises(tfdp.TfdpError):
-        tfdp.Batch([g1, g1], [tfdp.params_default(k_interp=3), tfdp.params_default(k_interp=2)])
     bad = (10, [[0, 0]], np.zeros((10, 2), np.float32))
     with pytest.raises(tfdp.TfdpError) as ei:
         tfdp.Batch([g1, bad])

@@ -343,6 +343,25 @@ def test_two_connected_nodes_reach_equilibrium(tfdp, mode):
         assert abs(d - np.linalg.norm(ref[0] - ref[1])) < 1e-4
 
 
+def test_set_params_to_a_smaller_arena_resets_the_visit_order(tfdp):
+    """A parameter change that shrinks the FFT arena (k = 1 -> 2 at the same cap: fewer
+    boxes, same FFT size) gets a new arena that the allocator may place at the old
+    address; the visit order must still restart from the caller order."""
+    rng = np.random.default_rng(17)
+    n = 1225
+    e = synth.lattice(35, 35)
+    xy = synth.uniform_positions(n, 17.5, rng)
+    with tfdp.Graph(n, e, xy, _params(tfdp, k_interp=1, grid_max=64)) as g:
+        g.eval_forces()
+        for k in (2, 3, 1, 2):
+            g.set_params(k_interp=k, grid_max=64)
+            fr, _ = g.eval_forces()
+            st = g.stats()
+            assert st["device_flags"] == 0
+            _, ref = _oracle_fft(xy, st, 2.0, k, 64, 1)
+            assert rel_l2(fr, ref) <= FORCE_TOL, k
+
+
 def test_set_positions_and_iteration_counter(tfdp):
     rng = np.random.default_rng(8)
     n = 1000
