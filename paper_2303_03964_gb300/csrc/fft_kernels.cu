@@ -227,14 +227,18 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
+    // sizes whose sequence fills the CTA keep one channel in registers at a time
+    constexpr bool kSeq = RegGeom<LOGP>::T > 512;
     if ((int)blockIdx.x < data_blocks) {
-        rows_fwd_body<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
+        if constexpr (kSeq) rows_fwd_body_seq<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
+        else rows_fwd_body<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
     } else {
         if (st->spec_dirty == 0) return;
         KernelSource ks;
         ks.P = 1 << LOGP;
         ks.bind(st, prm);
-        rows_fwd_body<LOGP>(ks, ks.P, blockIdx.x - data_blocks, S1, 1 << LOGP, tw, sm);
+        if constexpr (kSeq) rows_fwd_body_seq<LOGP>(ks, ks.P, blockIdx.x - data_blocks, S1, 1 << LOGP, tw, sm);
+        else rows_fwd_body<LOGP>(ks, ks.P, blockIdx.x - data_blocks, S1, 1 << LOGP, tw, sm);
     }
 }
 
@@ -246,7 +250,11 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
-    cols_body<LOGP>(blockIdx.x, T1, T2, ystride, specK, specHx, specHy, S1, tw, st->grid.G, st->spec_dirty, sm);
+    if constexpr (RegGeom<LOGP>::T > 512)
+        cols_body_seq<LOGP>(blockIdx.x, T1, T2, ystride, specK, specHx, specHy, S1, tw, st->grid.G, st->spec_dirty,
+                            sm);
+    else
+        cols_body<LOGP>(blockIdx.x, T1, T2, ystride, specK, specHx, specHy, S1, tw, st->grid.G, st->spec_dirty, sm);
 }
 
 template <int LOGP>
@@ -256,7 +264,8 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
-    rows_inv_body<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
+    if constexpr (RegGeom<LOGP>::T > 512) rows_inv_body_seq<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
+    else rows_inv_body<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -269,7 +278,7 @@ struct FftGeom {
     static constexpr size_t cols_smem = (size_t)3 * padded_len(P) * sizeof(float2);
 };
 
-constexpr int kMaxRegLogP = 12;  // register-resident path up to P = 4096
+constexpr int kMaxRegLogP = 13;  // register-resident path up to P = 8192 (one channel at a time there)
 
 template <int LOGP>
 static cudaError_t set_attrs() {

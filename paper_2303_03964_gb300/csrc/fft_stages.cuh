@@ -292,4 +292,171 @@ __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict_
     }
 }
 
+// ---------------------------------------------------------------- one channel at a time
+// The same three stages for sizes whose T = P/8 threads per sequence fill a whole CTA
+// (P = 8192: 1024 threads, at most 64 registers each): each thread keeps the eight values
+// of one channel in registers at a time, and the three channels of a row pair or column
+// sit in three shared-memory slices of P values. A transform uses its own slice for its
+// exchanges, and the last exchange of a forward transform reads (and the first of an
+// inverse writes) exactly the MF positions 8t .. 8t+7 of its thread, so the results can
+// be parked in, and taken back from, the thread's own MF positions without a barrier.
+
+template <int LOGP, class Src>
+__device__ __forceinline__ void rows_fwd_body_seq(const Src& src, int nrows, int blk, float2* __restrict__ out,
+                                                  int ystride, const float2* __restrict__ tw, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
+    static_assert(Gm::RG == 1, "one row pair per CTA");
+    const int G = nrows;
+    const int y0 = 2 * blk;
+    if (y0 >= G) return;
+    const int t = threadIdx.x;
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2* sl = sm + (size_t)c * P;
+        float2 v[1][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int x = t + r * T;
+            v[0][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+        }
+        reg_fft_forward<LOGP, 1>(v, sl, tw, t);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sl[swz(8 * t + r)] = v[0][r];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = split_freq<LOGP>(idx - c * NH);
+        const float2* seq = sm + (size_t)c * P;
+        const float2 Z = seq[swz(pos_of_freq<LOGP>(kx))], W = seq[swz(pos_of_freq<LOGP>((P - kx) & (P - 1)))];
+        reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + y0)[0] =
+            make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+    }
+}
+
+template <int LOGP>
+__device__ __forceinline__ void cols_body_seq(int kx, const float2* __restrict__ T1, float2* __restrict__ T2,
+                                              int ystride, float* __restrict__ specK, float* __restrict__ specHx,
+                                              float* __restrict__ specHy, const float2* __restrict__ S1,
+                                              const float2* __restrict__ tw, int G, int spec_dirty, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
+    static_assert(Gm::CG == 1, "one column per CTA");
+    const int t = threadIdx.x;
+    const size_t so = (size_t)kx * P + 8 * t;
+    if (spec_dirty) {
+        // rebuild: forward transforms along y of the row-transformed kernel samples
+        const float inv = 1.0f / ((float)P * (float)P);
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            float2 v[1][8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) v[0][r] = S1[((size_t)c * NH + kx) * P + t + r * T];
+            reg_fft_forward<LOGP, 1>(v, sm + (size_t)c * P, tw, t);
+            float o[8];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) o[r] = (c == 0 ? v[0][r].x : v[0][r].y) * inv;
+            float* dst = (c == 0 ? specK : (c == 1 ? specHx : specHy)) + so;
+            reinterpret_cast<float4*>(dst)[0] = make_float4(o[0], o[1], o[2], o[3]);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(o[4], o[5], o[6], o[7]);
+        }
+        __syncthreads();  // the slices are reused by the data transforms
+    }
+    // forward transforms of rho, m^x, m^y, each parked at its thread's MF positions
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2* sl = sm + (size_t)c * P;
+        float2 v[1][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = t + r * T;
+            v[0][r] = (y < G) ? T1[((size_t)c * NH + kx) * ystride + y] : make_float2(0.f, 0.f);
+        }
+        reg_fft_forward<LOGP, 1>(v, sl, tw, t);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sl[swz(8 * t + r)] = v[0][r];
+    }
+    // spectral product at this thread's own positions, four at a time
+    float2* s0 = sm;
+    float2* s1 = sm + P;
+    float2* s2 = sm + 2 * P;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float4 Kq = reinterpret_cast<const float4*>(specK + so)[h];
+        const float4 Xq = reinterpret_cast<const float4*>(specHx + so)[h];
+        const float4 Yq = reinterpret_cast<const float4*>(specHy + so)[h];
+        const float K4[4] = {Kq.x, Kq.y, Kq.z, Kq.w}, X4[4] = {Xq.x, Xq.y, Xq.z, Xq.w},
+                    Y4[4] = {Yq.x, Yq.y, Yq.z, Yq.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int a = swz(8 * t + 4 * h + q);
+            const float2 rr = s0[a], mx = s1[a], my = s2[a];
+            const float K = K4[q], hx = X4[q], hy = Y4[q];
+            s0[a] = make_float2(K * rr.x, K * rr.y);
+            s1[a] = make_float2(-hx * rr.y - K * mx.x, hx * rr.x - K * mx.y);
+            s2[a] = make_float2(-hy * rr.y - K * my.x, hy * rr.x - K * my.y);
+        }
+    }
+    // inverse transforms, rows y < G to T2
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2* sl = sm + (size_t)c * P;
+        float2 v[1][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[0][r] = sl[swz(8 * t + r)];
+        reg_fft_inverse<LOGP, 1>(v, sl, tw, t);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = t + r * T;
+            if (y < G) T2[((size_t)c * NH + kx) * ystride + y] = v[0][r];
+        }
+    }
+}
+
+template <int LOGP>
+__device__ __forceinline__ void rows_inv_body_seq(int blk, const float2* __restrict__ T2, int ystride,
+                                                  float4* __restrict__ gout, int Gs, const float2* __restrict__ tw,
+                                                  int G, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, NH = P / 2 + 1;
+    static_assert(Gm::RG == 1, "one row pair per CTA");
+    const int y0 = 2 * blk;
+    if (y0 >= G) return;
+    // Z_k = A_k + i B_k for the two real rows of the pair, both halves of the spectrum
+    for (int idx = threadIdx.x; idx < 3 * NH; idx += blockDim.x) {
+        const int c = idx / NH;
+        const int kx = split_freq<LOGP>(idx - c * NH);
+        float4 x = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + y0)[0];
+        if (y0 + 1 >= G) { x.z = 0.f; x.w = 0.f; }  // row past G: never written
+        float2* seq = sm + (size_t)c * P;
+        seq[swz(pos_of_freq<LOGP>(kx))] = make_float2(x.x - x.w, x.y + x.z);
+        if (kx != 0 && kx != P / 2) seq[swz(pos_of_freq<LOGP>((P - kx) & (P - 1)))] = make_float2(x.x + x.w, x.z - x.y);
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    // inverse transforms one channel at a time; each result is parked at the thread's
+    // natural-order positions t + r T of its slice (read by this thread only)
+#pragma unroll 1
+    for (int c = 0; c < 3; ++c) {
+        float2* sl = sm + (size_t)c * P;
+        float2 v[1][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[0][r] = sl[swz(8 * t + r)];
+        reg_fft_inverse<LOGP, 1>(v, sl, tw, t);
+        __syncthreads();  // the last exchange's reads are done before the slice is overwritten
+#pragma unroll
+        for (int r = 0; r < 8; ++r) sl[swz(t + r * T)] = v[0][r];
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int x = t + r * T;
+        if (x >= G) continue;
+        const int a = swz(x);
+        const float2 A = sm[a], X = sm[P + a], Y = sm[2 * P + a];
+        if (y0 < G) gout[(size_t)y0 * Gs + x] = make_float4(A.x, X.x, Y.x, 0.0f);
+        if (y0 + 1 < G) gout[(size_t)(y0 + 1) * Gs + x] = make_float4(A.y, X.y, Y.y, 0.0f);
+    }
+}
+
 }  // namespace tfdp

@@ -601,11 +601,10 @@ tfdp_status enqueue_step(tfdp_graph* g, cudaStream_t s, int advance, int eval, i
 // Kernels launched per iteration (count of the launches above).
 int kernels_per_iteration(const tfdp_graph* g) {
     // FFT: attraction, grid + bin + scan + scatter, spread, rows, cols, rows, gather +
-    // update; two more spectrum kernels for the shared-memory FFT (P = 8192)
+    // update (every FFT size runs the register-resident kernels, which build the
+    // spectrum inside the row and column passes)
     if (g->params.rep_mode == TFDP_REP_EXACT) return 2;
-    const int k = g->k_now();
-    const int lp = (k >= 1 && k <= kMaxK && g->logP_k[k]) ? g->logP_k[k] : g->logP;
-    return (1 + 4 + 1 + 1 + 1 + 1 + 1) + (lp > 12 ? 2 : 0);
+    return 1 + 4 + 1 + 1 + 1 + 1 + 1;
 }
 
 long long exec_key_of(const tfdp_graph* g, int k) {

@@ -125,7 +125,7 @@ def inverse(v, LOGN):
     return out
 
 
-@pytest.mark.parametrize("LOGN", [7, 8, 9, 10, 11])
+@pytest.mark.parametrize("LOGN", [7, 8, 9, 10, 11, 13])
 def test_forward_is_a_dft_in_digit_reversed_order_and_inverse_undoes_it(LOGN):
     N = 1 << LOGN
     rng = np.random.default_rng(LOGN)
@@ -157,7 +157,7 @@ def test_mappings_are_permutations_and_swizzle_stays_in_block(LOGN):
     assert all(swz(i) // 16 == i // 16 for i in range(N))
 
 
-@pytest.mark.parametrize("LOGN", [7, 10, 11, 12])
+@pytest.mark.parametrize("LOGN", [7, 10, 11, 12, 13])
 def test_each_exchange_writes_what_its_thread_read_last(LOGN):
     # forward exchanges read mapping p and the next one writes mapping p; the inverse
     # walks them backwards; so a thread only overwrites addresses it has read itself
