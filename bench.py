@@ -392,10 +392,8 @@ def serving_measurement(jobs=200, rate=20.0, updates=5, init_iters=300, upd_iter
 
 
 def stage_kernel(stage, P):
-    """Kernel of a single-kernel stage: the register-resident FFT kernels for P <= 4096,
-    the shared-memory ones above."""
-    if P > 4096 and stage in ("rows_fwd", "cols", "rows_inv"):
-        return {"rows_fwd": "k_rows_fwd", "cols": "k_cols", "rows_inv": "k_rows_inv"}[stage]
+    """Kernel of a single-kernel stage (every FFT size runs the register-resident FFT
+    kernels; P = 8192 keeps one channel in registers at a time)."""
     return STAGE_KERNEL[stage]
 
 
