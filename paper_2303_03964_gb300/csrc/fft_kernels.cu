@@ -218,17 +218,27 @@ __global__ void __launch_bounds__(256) k_rows_inv(const float2* __restrict__ T2,
     }
 }
 
+// Row passes that keep one channel in registers at a time (the *_seq bodies): P = 8192,
+// whose sequence fills a CTA. (At P = 2048 the same bodies at four CTAs per SM, one wave
+// for the 512 row pairs of a 1023-row grid, measured 4 % slower than three channels at
+// three CTAs per SM.)
+template <int LOGP>
+struct SeqRows {
+    static constexpr bool value = RegGeom<LOGP>::T > 512;
+    static constexpr int min_blocks = RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 3 : 1;
+};
+
 // Blocks [0, data_blocks): rows of the spread grid into T1. Blocks after that: rows of
 // the sampled kernels into S1, only in an iteration that rebuilds the spectrum.
 template <int LOGP>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 3 : 1)
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, SeqRows<LOGP>::min_blocks)
     k_rows_fwd_r(GridSource gsrc, int data_blocks, float2* __restrict__ T1, int ystride, float2* __restrict__ S1,
                  const float2* __restrict__ tw, const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     // sizes whose sequence fills the CTA keep one channel in registers at a time
-    constexpr bool kSeq = RegGeom<LOGP>::T > 512;
+    constexpr bool kSeq = SeqRows<LOGP>::value;
     if ((int)blockIdx.x < data_blocks) {
         if constexpr (kSeq) rows_fwd_body_seq<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
         else rows_fwd_body<LOGP>(gsrc, st->grid.G, blockIdx.x, T1, ystride, tw, sm);
@@ -258,13 +268,13 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<
 }
 
 template <int LOGP>
-__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RegGeom<LOGP>::T * RegGeom<LOGP>::RG <= 256 ? 3 : 1)
+__global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, SeqRows<LOGP>::min_blocks)
     k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
                  const float2* __restrict__ tw, const DevState* __restrict__ st) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
-    if constexpr (RegGeom<LOGP>::T > 512) rows_inv_body_seq<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
+    if constexpr (SeqRows<LOGP>::value) rows_inv_body_seq<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
     else rows_inv_body<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
 }
 

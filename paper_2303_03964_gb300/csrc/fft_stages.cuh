@@ -84,17 +84,24 @@ struct RegGeom {
 };
 
 // Frequency kx handled by split index j (0 <= j <= P/2) in the half-spectrum passes of
-// the row kernels: a bijection that gives the lanes of a warp frequencies P/64 apart.
-// Their digit-reversed positions (pos_of_freq) then differ in the low digits, i.e. fall
-// in different shared-memory banks; consecutive frequencies would all share one bank
-// pair, since the swizzle only mixes the low digits.
+// the row kernels, a bijection chosen so that the digit-reversed positions (pos_of_freq)
+// of the frequencies a half-warp touches fall in different shared-memory banks
+// (consecutive frequencies would all share one bank pair, since the swizzle only mixes
+// the low digits). Two maps: lane l of each half-warp takes kx = l P/32 + j div 16
+// (every half-warp access conflict-free at P = 128, 256, 1024, 2048, 8192), or the lanes
+// of a warp take frequencies P/64 apart (better at P = 512 and 4096, where the first map
+// puts pairs of lanes on one bank pair). A bank model of both maps is in the CPU tests.
 template <int LOGP>
 __device__ __forceinline__ int split_freq(int j) {
     static_assert(LOGP >= 6, "split_freq needs P / 2 to be a multiple of 32");
     constexpr int H = 1 << (LOGP - 1);  // P / 2
     if (j >= H) return j;               // the Nyquist bin
-    constexpr int R = H / 32;
-    return (j & 31) * R + (j >> 5);
+    if constexpr (LOGP == 9 || LOGP == 12) {
+        constexpr int R = H / 32;
+        return (j & 31) * R + (j >> 5);
+    } else {
+        return (j & 15) * (H / 16) + (j >> 4);
+    }
 }
 
 // Forward row transforms of row block `blk` (2 RG rows x 3 channels) of a source into

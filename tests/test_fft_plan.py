@@ -176,15 +176,64 @@ def test_each_exchange_writes_what_its_thread_read_last(LOGN):
     assert seq[len(fwd) - 1][1] == last and seq[len(fwd)][0] == last
 
 
-def split_freq(LOGP, j):
+def split_warp(LOGP, j):
+    """Lanes of a warp take frequencies P/64 apart."""
     H = 1 << (LOGP - 1)
     if j >= H:
         return j
-    R = H // 32
-    return (j & 31) * R + (j >> 5)
+    return (j & 31) * (H // 32) + (j >> 5)
+
+
+def split_half(LOGP, j):
+    """Lane l of each half-warp takes kx = l P/32 + j div 16."""
+    H = 1 << (LOGP - 1)
+    if j >= H:
+        return j
+    return (j & 15) * (H // 16) + (j >> 4)
+
+
+def split_freq(LOGP, j):
+    # the map the row kernels use at each FFT size
+    return split_warp(LOGP, j) if LOGP in (9, 12) else split_half(LOGP, j)
 
 
 @pytest.mark.parametrize("LOGP", [7, 8, 9, 10, 11, 12, 13])
 def test_split_freq_is_a_bijection_of_the_half_spectrum(LOGP):
     H = 1 << (LOGP - 1)
     assert sorted(split_freq(LOGP, j) for j in range(H + 1)) == list(range(H + 1))
+
+
+def split_wavefronts(mapf, LOGP):
+    """Shared-memory wavefronts of the split pass of one row pair (three channels, the
+    accesses at pos(kx) and at pos(P - kx)): per half-warp, the largest number of distinct
+    8-byte words that share a bank pair."""
+    P = 1 << LOGP
+    NH = P // 2 + 1
+    total = 0
+    for c in range(3):
+        for w0 in range(0, NH, 32):
+            for mirror in (False, True):
+                for half in (0, 16):
+                    banks = {}
+                    for lane in range(half, half + 16):
+                        j = w0 + lane
+                        if j >= NH:
+                            continue
+                        kx = mapf(LOGP, j)
+                        q = (P - kx) % P if mirror else kx
+                        a = c * P + swz(pos_of_freq(LOGP, q))
+                        banks.setdefault(a % 16, set()).add(a)
+                    total += max((len(v) for v in banks.values()), default=0)
+    return total
+
+
+@pytest.mark.parametrize("LOGP", [7, 8, 9, 10, 11, 12, 13])
+def test_split_map_is_the_better_of_the_two_for_the_banks(LOGP):
+    used = split_wavefronts(split_freq, LOGP)
+    assert used <= min(split_wavefronts(split_warp, LOGP), split_wavefronts(split_half, LOGP))
+    # within 2 % of the conflict-free count (two accesses per frequency, 16 per wavefront)
+    # except at P = 512 and 4096, where neither map reaches it
+    ideal = 3 * 2 * sum((min(32, (P := 1 << LOGP) // 2 + 1 - w0) + 15) // 16
+                        for w0 in range(0, (1 << LOGP) // 2 + 1, 32))
+    if LOGP not in (9, 12):
+        assert used <= 1.02 * ideal + 6, (used, ideal)
