@@ -58,9 +58,9 @@ WORKLOADS = {
 # unchanged (sha256 over STAGE_SOURCES). Captured with
 #   ncu --set full --clock-control none -k regex:k_cols_r -s 2 -c 1 -o prof_k_cols_r
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-batch --no-serving
-#       --no-dynamic-k --no-quality --no-workloads
+#       --no-dynamic-k --no-quality --no-workloads --no-mixed
 NCU_TRAFFIC = {
-    ("lattice_1m", "cols"): {"bytes": 50457344 + 1148160, "sha": "23d80cde29f93170"},
+    ("lattice_1m", "cols"): {"bytes": 50455808 + 887808, "sha": "3a29e7ed6b06b0f6"},
 }
 
 # Stages timed by the library that are ONE kernel on the critical path, and that kernel
