@@ -60,7 +60,10 @@ typedef enum {
 /* Arithmetic of the grid convolution (the FFT step of Sec. 3.4). */
 typedef enum {
     TFDP_PREC_FP32 = 0,  /* FP32 spread, FFT and interpolation */
-    TFDP_PREC_BF16X3 = 1 /* reserved: BF16 split-precision tensor-core convolution */
+    TFDP_PREC_BF16X3 = 1 /* the transforms along y and the spectral product as BF16
+                            split-precision tensor-core products (hi x hi + hi x lo +
+                            lo x hi, FP32 accumulation); FFT size 2048 only (grid_max
+                            513..1024) and a fixed k, else TFDP_ERR_PARAM_RANGE */
 } tfdp_precision;
 
 /* Box side of the interpolation grid, Sec. 3.4 ("Choices of k"). Both policies take
