@@ -148,6 +148,44 @@ __device__ __forceinline__ void rows_fwd_body(const Src& src, int nrows, int blk
     }
 }
 
+// Channel c only of row block `blk` (2 RG rows): the same transform and split as
+// rows_fwd_body computes for that channel, for launches with one CTA per (row block,
+// channel); sm holds RG sequences of P values.
+template <int LOGP, class Src>
+__device__ __forceinline__ void rows_fwd_body_ch(const Src& src, int c, int nrows, int blk, float2* __restrict__ out,
+                                                 int ystride, const float2* __restrict__ tw, float2* sm) {
+    using Gm = RegGeom<LOGP>;
+    constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    const int G = nrows;
+    const int ybase = blk * (2 * RG);
+    if (ybase >= G) return;
+    const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
+    const int y0 = ybase + 2 * lr;
+    float2* smr = sm + (size_t)lr * P;
+    float2 v[1][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int x = t + r * T;
+        v[0][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+    }
+    reg_fft_forward<LOGP, 1>(v, smr, tw, t);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) smr[swz(8 * t + r)] = v[0][r];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NH; idx += blockDim.x) {
+        const int kx = split_freq<LOGP>(idx);
+        const int pk = swz(pos_of_freq<LOGP>(kx));
+        const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
+        float4* dst = reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + ybase);
+#pragma unroll
+        for (int q = 0; q < RG; ++q) {
+            const float2* seq = sm + (size_t)q * P;
+            const float2 Z = seq[pk], W = seq[pn];
+            dst[q] = make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+        }
+    }
+}
+
 // Column block cblk (CG columns kx): forward along y of (rho, m^x, m^y) from T1,
 // spectral product A = K rho, O^x = i hx rho - K m^x, O^y = i hy rho - K m^y, inverse along
 // y, rows y < G to T2. When spec_dirty, the kernel spectra of these columns are first
@@ -164,9 +202,11 @@ __device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T
     const bool valid = kx < NH;
     float2* smc = sm + (size_t)lc * 3 * P;
     float2 v[3][8];
-    // kernel spectra at this thread's output positions 8t .. 8t+7 (digit-reversed order)
+    // kernel spectra at this thread's output positions 8t .. 8t+7 (digit-reversed order),
+    // stored per column as two float4 planes of T entries (positions 8t + 0..3 at t,
+    // 8t + 4..7 at T + t), so that a warp's loads are contiguous
     float K[8], hx[8], hy[8];
-    const size_t so = (size_t)(valid ? kx : 0) * P + 8 * t;
+    const size_t so = (size_t)(valid ? kx : 0) * 2 * T + t;  // in float4 units
     if (spec_dirty) {
         // rebuild: forward transform along y of the row-transformed kernel samples
 #pragma unroll
@@ -183,14 +223,14 @@ __device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T
             hy[r] = v[2][r].y * inv;
         }
         if (valid) {
-            float4* pK = reinterpret_cast<float4*>(specK + so);
-            float4* pX = reinterpret_cast<float4*>(specHx + so);
-            float4* pY = reinterpret_cast<float4*>(specHy + so);
+            float4* pK = reinterpret_cast<float4*>(specK) + so;
+            float4* pX = reinterpret_cast<float4*>(specHx) + so;
+            float4* pY = reinterpret_cast<float4*>(specHy) + so;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                pK[h] = make_float4(K[4 * h], K[4 * h + 1], K[4 * h + 2], K[4 * h + 3]);
-                pX[h] = make_float4(hx[4 * h], hx[4 * h + 1], hx[4 * h + 2], hx[4 * h + 3]);
-                pY[h] = make_float4(hy[4 * h], hy[4 * h + 1], hy[4 * h + 2], hy[4 * h + 3]);
+                pK[h * T] = make_float4(K[4 * h], K[4 * h + 1], K[4 * h + 2], K[4 * h + 3]);
+                pX[h * T] = make_float4(hx[4 * h], hx[4 * h + 1], hx[4 * h + 2], hx[4 * h + 3]);
+                pY[h * T] = make_float4(hy[4 * h], hy[4 * h + 1], hy[4 * h + 2], hy[4 * h + 3]);
             }
         }
         __syncthreads();  // shared memory is reused by the data transform
@@ -207,12 +247,12 @@ __device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T
         // spectra at the output positions; loaded here (not before the transform) to keep
         // them out of the registers the transform needs; after a rebuild this re-reads
         // what this thread just wrote
-        const float4* pK = reinterpret_cast<const float4*>(specK + so);
-        const float4* pX = reinterpret_cast<const float4*>(specHx + so);
-        const float4* pY = reinterpret_cast<const float4*>(specHy + so);
+        const float4* pK = reinterpret_cast<const float4*>(specK) + so;
+        const float4* pX = reinterpret_cast<const float4*>(specHx) + so;
+        const float4* pY = reinterpret_cast<const float4*>(specHy) + so;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const float4 a = pK[h], b = pX[h], d = pY[h];
+            const float4 a = pK[h * T], b = pX[h * T], d = pY[h * T];
             K[4 * h] = a.x; K[4 * h + 1] = a.y; K[4 * h + 2] = a.z; K[4 * h + 3] = a.w;
             hx[4 * h] = b.x; hx[4 * h + 1] = b.y; hx[4 * h + 2] = b.z; hx[4 * h + 3] = b.w;
             hy[4 * h] = d.x; hy[4 * h + 1] = d.y; hy[4 * h + 2] = d.z; hy[4 * h + 3] = d.w;

@@ -30,11 +30,10 @@ struct FftLaunch {
     const DevParams* prm;
 };
 
-cudaError_t launch_spectrum(const FftLaunch& a, cudaStream_t s);   // 2 kernels
+cudaError_t launch_spectrum(const FftLaunch& a, cudaStream_t s);   // no kernel (rebuilt by the passes below)
 cudaError_t launch_rows_fwd(const FftLaunch& a, cudaStream_t s);   // 1 kernel
 cudaError_t launch_cols(const FftLaunch& a, cudaStream_t s);       // 1 kernel
 cudaError_t launch_rows_inv(const FftLaunch& a, cudaStream_t s);   // 1 kernel
-int fft_rows_per_cta(int logP);
 // BF16x3 tensor-core column stage (cols_tc.cu), P = 2048 only: the 96 KB DFT-matrix image
 // (build_tc_constants, uploaded once per arena), natural-order kernel spectra
 // (3 x (P/2+1) x P floats, rebuilt in place when the spectrum is stale), 1 kernel.
