@@ -25,6 +25,8 @@
 // iteration whose box side, gamma, k or P changed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "fft_reg.cuh"
@@ -56,16 +58,19 @@ struct RowsFwdGeom {
 };
 
 // Blocks [0, ch data_blocks): channel b % ch of row block b / ch of the spread grid into
-// T1. Blocks after that: the same for the rows of the sampled kernels into S1, only in
-// an iteration that rebuilds the spectrum.
+// T1. The ch spec_blocks blocks after that: the same for the rows of the sampled kernels
+// into S1, each taking every spec_blocks-th row block, only in an iteration that rebuilds
+// the spectrum (otherwise they return at once, so they are kept few).
 template <int LOGP>
 __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RowsFwdGeom<LOGP>::min_blocks)
-    k_rows_fwd_r(GridSource gsrc, int data_blocks, float2* __restrict__ T1, int ystride, float2* __restrict__ S1,
-                 const float2* __restrict__ tw, const DevState* __restrict__ st, const DevParams* __restrict__ prm) {
+    k_rows_fwd_r(GridSource gsrc, int data_blocks, int spec_blocks, float2* __restrict__ T1, int ystride,
+                 float2* __restrict__ S1, const float2* __restrict__ tw, const DevState* __restrict__ st,
+                 const DevParams* __restrict__ prm) {
     extern __shared__ float2 sm[];
     pdl_wait();
     pdl_trigger();
     using Fg = RowsFwdGeom<LOGP>;
+    constexpr int P = 1 << LOGP;
     const int rb = (int)blockIdx.x / Fg::ch;
     const int c = (int)blockIdx.x - rb * Fg::ch;
     if (rb < data_blocks) {
@@ -74,10 +79,14 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RowsFwdG
     } else {
         if (st->spec_dirty == 0) return;
         KernelSource ks;
-        ks.P = 1 << LOGP;
+        ks.P = P;
         ks.bind(st, prm);
-        if constexpr (Fg::seq) rows_fwd_body_seq<LOGP>(ks, ks.P, rb - data_blocks, S1, 1 << LOGP, tw, sm);
-        else rows_fwd_body_ch<LOGP>(ks, c, ks.P, rb - data_blocks, S1, 1 << LOGP, tw, sm);
+        constexpr int kRowBlocks = P / (2 * RegGeom<LOGP>::RG);
+        for (int sb = rb - data_blocks; sb < kRowBlocks; sb += spec_blocks) {
+            if constexpr (Fg::seq) rows_fwd_body_seq<LOGP>(ks, P, sb, S1, P, tw, sm);
+            else rows_fwd_body_ch<LOGP>(ks, c, P, sb, S1, P, tw, sm);
+            __syncthreads();  // the next row block's exchanges reuse sm
+        }
     }
 }
 
@@ -153,9 +162,10 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
     gs.gin = a.gin;
     gs.Gs = a.Gs;
     const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-    const int spec_blocks = Rg::P / (2 * Rg::RG);
+    // spectrum row blocks: about two per SM and channel, each looping over its share
+    const int spec_blocks = std::min(Rg::P / (2 * Rg::RG), 2 * 152);
     return launch_pdl(k_rows_fwd_r<LOGP>, Fg::ch * (blocks + spec_blocks), Rg::T * Rg::RG, Fg::smem, s, gs, blocks,
-                      a.T1, a.ystride, a.S1, a.tw, (const DevState*)a.st, (const DevParams*)a.prm);
+                      spec_blocks, a.T1, a.ystride, a.S1, a.tw, (const DevState*)a.st, (const DevParams*)a.prm);
 }
 
 template <int LOGP>
