@@ -114,6 +114,44 @@ def test_fft_forces_small(tfdp, k, policy):
     assert rel_l2(fa, oracle.attraction(e, xy.astype(np.float64), 0.1, 8.0)) <= FORCE_TOL
 
 
+def _boundary_sides():
+    """Layout sides L at the snap rule's decision boundaries (N_int h = L exactly, one FP32
+    step either side), at powers of two of L / N_int, and log-uniform in [1e-3, 1e4]."""
+    out = []
+    for n in (50, 97, 113):
+        for e in range(-6, 1):
+            for j in range(17):
+                L = np.float32(n * (16 + j) * 2.0 ** (e - 5))
+                out += [(n, L), (n, np.nextafter(L, np.float32(np.inf))), (n, np.nextafter(L, np.float32(0)))]
+    rng = np.random.default_rng(77)
+    out += [(50, np.float32(x)) for x in np.exp(rng.uniform(np.log(1e-3), np.log(1e4), 300))]
+    return out
+
+
+@pytest.mark.parametrize("k,policy", [(3, 1), (2, 1), (1, 1), (3, 0)])
+def test_grid_decision_matches_oracle_at_snap_boundaries(tfdp, k, policy):
+    """Sec. 3.4 grid rule: N_int, h and the origin decided on the device equal the oracle's
+    FP64 decision bit for bit, including sides where N_int h = L exactly (the first passing
+    snap candidate) and sides just above and below."""
+    sides = _boundary_sides()
+    rng = np.random.default_rng(k + 10 * policy)
+    xy = np.zeros((2, 2), np.float32)
+    with tfdp.Graph(2, np.zeros((0, 2), np.int32), xy, _params(tfdp, k_interp=k, grid_policy=policy)) as g:
+        nmin = None
+        for q, (n, L) in enumerate(sides):
+            if n != nmin:
+                g.set_params(_params(tfdp, k_interp=k, grid_policy=policy, n_int_min=n))
+                nmin = n
+            lo = np.float32(0.0) if q % 2 == 0 else np.float32(rng.uniform(-300, 300))
+            xy = np.array([[lo, lo], [lo + L, lo + L]], np.float32)
+            g.set_positions(xy)
+            g.eval_forces()
+            st = g.stats()
+            ref = oracle.grid_policy(xy, k, n, 1023, policy)
+            got = (st["grid_n_int"], st["grid_h"], st["grid_lo"])
+            assert got == (ref["n_int"], ref["h"], ref["lo"]), (q, n, float(L), float(lo), got, ref)
+
+
 @pytest.mark.parametrize("grid_max,k", [(40, 3), (100, 2), (255, 1), (511, 3), (1023, 2),
                                          (2047, 3), (4095, 3)])
 def test_fft_forces_every_fft_size(tfdp, grid_max, k):
