@@ -692,6 +692,7 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
             sampler.active = False
         sts = [b.stats(q) for q in range(len(graphs))]
         parts = b.num_parts()
+        phase_parts = b.phase_parts()
         b.close()
         # single-pass byte model of every graph's iteration at its own grid and FFT size
         model_bytes = sum(iteration_model_bytes(g[0], len(g[1]), st["grid_G"], st["fft_P"])
@@ -699,6 +700,9 @@ def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, samp
         mean_ms = statistics.fmean(ms)
         return {"value": total_n * len(ms) / (sum(ms) * 1e-3), "unit": UNIT, "ms_per_step": mean_ms,
                 "parts": parts, "cooperative_ctas": blocks,
+                "launch_shape": ("one launch per phase" if phase_parts == parts else
+                                 "one cooperative launch" if phase_parts == 0 else
+                                 "%d of %d parts one launch per phase" % (phase_parts, parts)),
                 "device_flags": max(st["device_flags"] for st in sts),
                 "iteration_roofline": {
                     "bytes_per_iteration": model_bytes, "achieved": model_bytes / (mean_ms * 1e-3) / 1e9,

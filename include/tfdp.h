@@ -262,12 +262,14 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
 tfdp_status tfdp_destroy_graph(tfdp_graph* g);
 
 /*
- * Batches: many independent graphs advanced together by cooperative persistent kernels
- * (Sec. 3.4 ibFFT path for every graph; the batching itself has no counterpart in the
- * paper). Graphs keep their own parameters, grids, spectra, state and iteration
- * counters; the arithmetic per graph is that of a single graph, so each graph's result
- * equals its solo run. Graphs are grouped into parts by (k_interp, FFT size); each call
- * runs one persistent launch per part, the parts one after another on the stream.
+ * Batches: many independent graphs advanced together (Sec. 3.4 ibFFT path for every
+ * graph; the batching itself has no counterpart in the paper). Graphs keep their own
+ * parameters, grids, spectra, state and iteration counters; the arithmetic per graph is
+ * that of a single graph, so each graph's result equals its solo run. Graphs are grouped
+ * into parts by (k_interp, FFT size); each call runs the parts one after another on the
+ * stream, each as nine launches per iteration (one per phase, every launch spanning all
+ * graphs of the part) or as one cooperative persistent launch for all its iterations
+ * (tfdp_batch_set_phase_launches, tfdp_batch_autotune).
  */
 typedef struct tfdp_batch tfdp_batch;
 
@@ -288,8 +290,8 @@ tfdp_status tfdp_batch_create(int32_t num_graphs, const int64_t* n, const int64_
                               const int32_t* const* edges, const float* const* xy0,
                               const tfdp_params* params, void* stream, tfdp_batch** out);
 
-/* Run `iters` iterations of every graph in one persistent launch (replayed from a
- * captured CUDA graph). Asynchronous on the batch's stream. */
+/* Run `iters` iterations of every graph (per part: 9 iters launches or one persistent
+ * launch, replayed from a captured CUDA graph). Asynchronous on the batch's stream. */
 tfdp_status tfdp_batch_iterate(tfdp_batch* b, int32_t iters);
 
 /* Forces of graph `graph` at the current positions (the whole batch is evaluated
@@ -337,10 +339,23 @@ tfdp_status tfdp_batch_plan(int32_t num_graphs, const int64_t* n, const int64_t*
                             double min_error_bound, int32_t probes, tfdp_params* out_params,
                             double* out_error);
 
-/* Launch-shape autotuner: times `trials` force evaluations of the whole batch for each
- * number of co-resident CTAs per SM the kernel allows and keeps the fastest
- * (*chosen_blocks, may be NULL, receives the CTA count). Synchronises; no node moves. */
+/* Launch-shape autotuner, per part: times `trials` force evaluations of the whole batch
+ * as one cooperative persistent launch at each number of co-resident CTAs per SM the
+ * kernel allows, and as nine ordinary launches per iteration (one per phase, one CTA per
+ * work item, each kernel at its own occupancy), and keeps the fastest. *chosen_blocks
+ * (may be NULL) receives the largest cooperative CTA count kept, 0 when every part runs
+ * per-phase launches. Before the first call every part runs per-phase launches.
+ * Synchronises; no node moves. */
 tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_blocks);
+
+/* Launch shape of every part: on = 1 one launch per phase, on = 0 the cooperative
+ * persistent launch (at the last CTA count the autotuner kept, else the occupancy
+ * limit). The results do not depend on it. TFDP_ERR_INVALID_ARG unless on is 0 or 1.
+ * Synchronises the batch's stream when the shape changes. */
+tfdp_status tfdp_batch_set_phase_launches(tfdp_batch* b, int32_t on);
+
+/* Number of parts that run one launch per phase, 0 for NULL. */
+int32_t tfdp_batch_phase_parts(const tfdp_batch* b);
 
 /*
  * Serving: interactive layout jobs with continuous batching. A job is a graph and a

@@ -1,13 +1,16 @@
-// batch.cu -- many graphs advanced together by one cooperative persistent kernel.
+// batch.cu -- many graphs advanced together, by one cooperative persistent kernel or by
+// one launch per phase.
 //
 // A batch holds B independent graphs in packed arenas (positions, CSR, sort buffers)
-// with per-graph parameters, state, grids and spectra. An iteration call runs `iters`
-// t-FDP iterations of every graph in a single launch: the kernel walks through the
-// nine phases of an iteration (grid policy; binning + attraction; per-graph scan;
-// scatter; spread; row / column / inverse-row FFT stages; back-projection + update),
-// each phase distributing (graph, item) work over all CTAs, with a grid-wide barrier
-// between phases. The per-node and per-transform arithmetic is the single-graph code
-// (node_dev.cuh, fft_stages.cuh), so every graph evolves as it would alone.
+// with per-graph parameters, state, grids and spectra. An iteration has nine phases
+// (grid policy; binning + attraction; per-graph scan; scatter; spread; row / column /
+// inverse-row FFT stages; back-projection + update), each distributing (graph, item)
+// work over CTAs. An iteration call runs `iters` iterations of every graph either in a
+// single cooperative launch, whose CTAs walk the phases with a grid-wide barrier between
+// them, or as nine ordinary launches per iteration with one CTA per item, each at its
+// own occupancy (captured in a CUDA graph); tfdp_batch_autotune times both. The per-node
+// and per-transform arithmetic is the single-graph code (node_dev.cuh, fft_stages.cuh),
+// so every graph evolves as it would alone.
 //
 // A batch is split into parts by (k, FFT size): each part is one such persistent launch
 // whose graphs share k and P (P >= 2 G_max - 1 for every graph of the part, so each
@@ -105,6 +108,8 @@ struct BatchPart {
     double* d_steps = nullptr;  // per-graph step tables, B x T_max
     int T_max = 0;
     int grid_blocks = 0;       // cooperative grid size
+    bool phases = true;        // one launch per phase (false: the cooperative persistent kernel)
+    BatchItems items{};        // items of each phase (per-phase launches)
     cudaGraphExec_t exec = nullptr;
     int exec_iters = -1;
     bool no_graph = false;
@@ -139,10 +144,26 @@ tfdp_status batch_sync_checked(BatchPart* b, int g0, int g1) {
 }
 
 cudaError_t batch_launch(const BatchPart* b, const BatchArgs& a, cudaStream_t s) {
+    if (b->phases) {
+        switch (b->k) {
+            case 1: return batch_phases_k<1>(b->logP, a, b->items, s);
+            case 2: return batch_phases_k<2>(b->logP, a, b->items, s);
+            case 3: return batch_phases_k<3>(b->logP, a, b->items, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (b->k) {
         case 1: return batch_launch_k<1>(b->logP, a, b->grid_blocks, s);
         case 2: return batch_launch_k<2>(b->logP, a, b->grid_blocks, s);
         case 3: return batch_launch_k<3>(b->logP, a, b->grid_blocks, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+cudaError_t batch_phases_attrs(const BatchPart* b) {
+    switch (b->k) {
+        case 1: return batch_phases_attrs_k<1>(b->logP);
+        case 2: return batch_phases_attrs_k<2>(b->logP);
+        case 3: return batch_phases_attrs_k<3>(b->logP);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -427,6 +448,8 @@ tfdp_status part_create(int32_t num_graphs, const int64_t* n, const int64_t* m, 
     if (st != TFDP_OK) return fail(st);
     int bps = 0;
     if ((e = batch_occupancy(b, &bps)) != cudaSuccess || bps < 1) return fail(bfail(e, "batch occupancy"));
+    if ((e = batch_phases_attrs(b)) != cudaSuccess) return fail(bfail(e, "batch phase kernels"));
+    b->items = BatchItems{pre_nodes.back(), pre_boxes.back(), pre_rows.back(), pre_cols.back()};
     int sms = 0;
     int dev = 0;
     cudaGetDevice(&dev);
@@ -555,27 +578,38 @@ tfdp_status part_autotune(BatchPart* b, int32_t trials, int32_t* chosen_blocks) 
     a.eval = 1;
     float best = 1e30f;
     int best_blocks = b->grid_blocks;
+    auto time_it = [&](float* ms) -> cudaError_t {
+        cudaError_t e = batch_launch(b, a, b->stream);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int t = 0; t < trials && e == cudaSuccess; ++t) e = batch_launch(b, a, b->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        return e;
+    };
+    b->phases = false;
     for (int c = 1; c <= bps; ++c) {
         b->grid_blocks = c * sms;
-        BK(batch_launch(b, a, b->stream));  // warm-up
-        BK(cudaEventRecord(e0, b->stream));
-        for (int t = 0; t < trials; ++t) BK(batch_launch(b, a, b->stream));
-        BK(cudaEventRecord(e1, b->stream));
-        BK(cudaEventSynchronize(e1));
         float ms = 0.0f;
-        BK(cudaEventElapsedTime(&ms, e0, e1));
+        BK(time_it(&ms));
         if (ms < best) {
             best = ms;
             best_blocks = c * sms;
         }
     }
+    // the other launch shape: one launch per phase
+    b->phases = true;
+    float ms_phases = 0.0f;
+    BK(time_it(&ms_phases));
+    b->phases = ms_phases < best;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->grid_blocks = best_blocks;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->exec_iters = -1;
-    if (chosen_blocks) *chosen_blocks = best_blocks;
+    b->no_graph = false;
+    if (chosen_blocks) *chosen_blocks = b->phases ? 0 : best_blocks;
     return TFDP_OK;
 }
 
@@ -724,6 +758,27 @@ tfdp_status tfdp_batch_autotune(tfdp_batch* b, int32_t trials, int32_t* chosen_b
 }
 
 int32_t tfdp_batch_num_parts(const tfdp_batch* b) { return b ? (int32_t)b->parts.size() : 0; }
+
+tfdp_status tfdp_batch_set_phase_launches(tfdp_batch* b, int32_t on) {
+    if (!b || (on != 0 && on != 1)) return TFDP_ERR_INVALID_ARG;
+    for (BatchPart* part : b->parts) {
+        if (part->phases == (on != 0)) continue;
+        BK(cudaStreamSynchronize(part->stream));
+        part->phases = on != 0;
+        if (part->exec) cudaGraphExecDestroy(part->exec);
+        part->exec = nullptr;
+        part->exec_iters = -1;
+        part->no_graph = false;
+    }
+    return TFDP_OK;
+}
+
+int32_t tfdp_batch_phase_parts(const tfdp_batch* b) {
+    int32_t c = 0;
+    if (b)
+        for (const BatchPart* part : b->parts) c += part->phases ? 1 : 0;
+    return c;
+}
 
 }  // extern "C"
 

@@ -97,6 +97,8 @@ _SIGS = {
     "tfdp_batch_destroy": ([_p], ctypes.c_int),
     "tfdp_batch_grid_blocks": ([_p], ctypes.c_int32),
     "tfdp_batch_autotune": ([_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "tfdp_batch_phase_parts": ([_p], ctypes.c_int32),
+    "tfdp_batch_set_phase_launches": ([_p, ctypes.c_int32], ctypes.c_int),
     "tfdp_batch_num_parts": ([_p], ctypes.c_int32),
     "tfdp_batch_plan": ([ctypes.c_int32, _p, _p, _p, _p, _p, ctypes.c_double, ctypes.c_double, ctypes.c_int32,
                          _p, _p], ctypes.c_int),
@@ -468,6 +470,14 @@ class Batch:
 
     def grid_blocks(self):
         return int(lib.tfdp_batch_grid_blocks(self._h))
+
+    def phase_parts(self):
+        """Parts that run one launch per phase (the rest: one cooperative launch)."""
+        return int(lib.tfdp_batch_phase_parts(self._h))
+
+    def set_phase_launches(self, on=True):
+        """One launch per phase (True) or the cooperative persistent launch (False)."""
+        _check(lib.tfdp_batch_set_phase_launches(self._h, 1 if on else 0), "tfdp_batch_set_phase_launches")
 
     def num_parts(self):
         return int(lib.tfdp_batch_num_parts(self._h))

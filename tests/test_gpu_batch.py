@@ -45,12 +45,17 @@ def tfdp():
     return t
 
 
+@pytest.mark.parametrize("phases", [True, False])
 @pytest.mark.parametrize("grid_max", [255, 100])
-def test_batch_forces_equal_solo(tfdp, grid_max):
+def test_batch_forces_equal_solo(tfdp, grid_max, phases):
+    """Both launch shapes (one launch per phase, one cooperative persistent launch) give
+    every graph its solo run's forces."""
     graphs = _mixed_graphs(9, 31 + grid_max)
     params = [tfdp.params_default(grid_max=grid_max, gamma=2.0 + 0.5 * (q % 3)) for q in range(len(graphs))]
     with tfdp.Batch(graphs, params) as b:
-        assert b.grid_blocks() > 0
+        assert b.grid_blocks() > 0 and b.phase_parts() == 1
+        b.set_phase_launches(phases)
+        assert b.phase_parts() == (1 if phases else 0)
         for q, (n, e, xy) in enumerate(graphs):
             fr_b, fa_b = b.eval_forces(q)
             with tfdp.Graph(n, e, xy, params[q]) as g:
@@ -65,11 +70,13 @@ def test_batch_forces_equal_solo(tfdp, grid_max):
             assert b.stats(q)["grid_G"] == st["grid_G"]
 
 
-def test_batch_layout_equals_solo(tfdp):
+@pytest.mark.parametrize("phases", [True, False])
+def test_batch_layout_equals_solo(tfdp, phases):
     graphs = _mixed_graphs(6, 77, nmin=500, nmax=3000)
     params = [tfdp.params_default(grid_max=255, total_iters=50) for _ in graphs]
     T = 8
     with tfdp.Batch(graphs, params) as b:
+        b.set_phase_launches(phases)
         b.iterate(3)
         b.iterate(T - 3)  # two launches (two captured graphs) in a row
         for q, (n, e, xy) in enumerate(graphs):
@@ -136,6 +143,12 @@ def test_batch_plan_meets_its_error_bound(tfdp):
     with tfdp.Batch(graphs, params) as b:
         b.iterate(2)
         b.synchronize()
+        # the launch-shape autotuner keeps either shape; the layout goes on from where it is
+        b.autotune(2)
+        assert 0 <= b.phase_parts() <= b.num_parts()
+        b.iterate(2)
+        b.synchronize()
+        assert all(b.stats(q)["iteration"] == 4 and b.stats(q)["device_flags"] == 0 for q in range(len(graphs)))
 
 
 def test_batch_rejects_dynamic_k_and_bad_graph(tfdp):
