@@ -656,7 +656,7 @@ def cpu_baseline(e, xy, spec, budget_s=15.0):
 
 
 def batched_measurement(args, stream, flush, steps, warmup, solo_sample=48, sampler=None):
-    """512 mixed graphs (n log-uniform in [1k, 50k]) advanced by persistent launches, with
+    """512 mixed graphs (n log-uniform in [1k, 50k]) advanced together as a batch, with
     every graph at the reference grid (k = 3, grid <= 255: P = 512) and with the grids the
     autotuner (tfdp_batch_plan) picks per graph by measured force error; against the same
     graphs run one at a time (a sample of them, reference grid)."""

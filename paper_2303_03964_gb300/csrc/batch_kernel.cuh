@@ -1,5 +1,5 @@
-// batch_kernel.cuh -- the cooperative persistent kernel of a batch of graphs and the
-// data it reads. The kernel is instantiated per k in batch_k1.cu, batch_k2.cu and
+// batch_kernel.cuh -- the kernels of a batch of graphs (per-phase and persistent) and the
+// data they read. The kernels are instantiated per k in batch_k1.cu, batch_k2.cu and
 // batch_k3.cu (which nvcc compiles in parallel); batch.cu holds the host side.
 //
 // An iteration is nine phases (grid policy; binning + attraction; per-graph scan;

@@ -1,6 +1,6 @@
 // fft_stages.cuh -- the three register-resident FFT stages of the grid interaction
 // (Sec. 3.4, second step) as device functions over one work item, shared by the
-// single-graph kernels (fft_kernels.cu) and the batched persistent kernel (batch.cu).
+// single-graph kernels (fft_kernels.cu) and the batch kernels (batch_kernel.cuh).
 //
 // The transforms evaluate the well-conditioned form of Eq. (Fr1)/(Fr2):
 //   A = K * rho,   O^x = (Delta_x K) * rho - K * m^x,   O^y likewise,

@@ -1,6 +1,6 @@
 // node_dev.cuh -- per-node device functions of the ibFFT path and the update, shared
-// by the single-graph kernels (node_kernels.cu) and the batched persistent kernel
-// (batch.cu) so that both compute identical per-node arithmetic.
+// by the single-graph kernels (node_kernels.cu) and the batch kernels
+// (batch_kernel.cuh) so that both compute identical per-node arithmetic.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -404,11 +404,12 @@ def batch_plan(graphs, base=None, max_error_ratio=1.5, min_error_bound=0.0, prob
 
 
 class Batch:
-    """Many graphs advanced together by persistent launches (wraps tfdp_batch).
+    """Many graphs advanced together (wraps tfdp_batch).
 
     ``graphs`` is a list of (n, edges (m x 2 int32), xy0 (n x 2 float32)); ``params`` is
     None (defaults) or one Params per graph; graphs with the same (k_interp, FFT size)
-    share one persistent launch (a part).
+    form a part, whose iterations run as one launch per phase (default) or as one
+    cooperative persistent launch (``set_phase_launches``, ``autotune``).
     """
 
     def __init__(self, graphs, params=None, stream=0):

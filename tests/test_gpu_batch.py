@@ -1,4 +1,4 @@
-"""Batched persistent launch: every graph of a batch must give the forces and the
+"""Batches: every graph of a batch must give the forces and the
 short layout of its solo run (and, through it, of the oracle)."""
 import numpy as np
 import pytest
@@ -89,7 +89,7 @@ def test_batch_layout_equals_solo(tfdp, phases):
 
 
 def test_batch_parts_of_mixed_k_and_fft_size_equal_solo(tfdp):
-    """Graphs with different k and grid caps run as several parts (one persistent launch
+    """Graphs with different k and grid caps run as several parts (one set of launches
     per (k, FFT size)); each graph still gives its solo run's forces and layout, and the
     oracle's ibFFT at its own grid."""
     graphs = _mixed_graphs(8, 91, nmin=400, nmax=5000)
