@@ -339,7 +339,7 @@ tfdp_status part_create(int32_t num_graphs, const int64_t* n, const int64_t* m, 
         G.nbox_max = n_int_max * n_int_max;
         pre_nodes.push_back(pre_nodes.back() + (G.n + kBChunk - 1) / kBChunk);
         pre_boxes.push_back(pre_boxes.back() + (G.nbox_max + kBChunk - 1) / kBChunk);
-        pre_rows.push_back(pre_rows.back() + (G.G_max + 2 * RG - 1) / (2 * RG) + b->P / (2 * RG));
+        pre_rows.push_back(pre_rows.back() + (G.G_max + 2 * RG - 1) / (2 * RG) + (spec_rows(b->P) + 2 * RG - 1) / (2 * RG));
         pre_cols.push_back(pre_cols.back() + (int)((NH + CG - 1) / CG));
         fft_off[(size_t)g] = fft_bytes;
         fft_bytes += up(sizeof(int) * (size_t)G.nbox_max, 256) + up(sizeof(int) * ((size_t)G.nbox_max + 1), 256) +

@@ -190,7 +190,7 @@ __device__ void tc_spectrum(int kx, const float2* __restrict__ S1, const float2*
     constexpr int P = kTcP, PL = padded_len(P);
     for (int idx = threadIdx.x; idx < 3 * P; idx += blockDim.x) {
         const int c = idx / P, y = idx - c * P;
-        sm[c * PL + spad(y)] = S1[((size_t)c * kTcNH + kx) * P + y];
+        sm[c * PL + spad(y)] = s1_row<P>(S1, c, kx, y);
     }
     __syncthreads();
     fft_forward<kTcLogP>(sm, 3, tw);

@@ -184,4 +184,21 @@ __device__ __forceinline__ int freq_of_pos(int p) {
     return k;
 }
 
+// ---------------------------------------------------------------- kernel-sample rows
+// Rows of the kernel samples that a spectrum rebuild transforms along x: 0 .. P/2. The
+// three kernels are even in D_y (K, D_x K) or odd (D_y K), so the row-transformed samples
+// of row P - y are those of row y, negated for channel 2; s1_row reads them that way.
+__host__ __device__ constexpr int spec_rows(int P) { return P / 2 + 1; }
+
+template <int P>
+__device__ __forceinline__ float2 s1_row(const float2* __restrict__ S1, int c, int kx, int y) {
+    const bool mirror = y > P / 2;
+    float2 w = S1[((size_t)c * (P / 2 + 1) + kx) * P + (mirror ? P - y : y)];
+    if (mirror && c == 2) {
+        w.x = -w.x;
+        w.y = -w.y;
+    }
+    return w;
+}
+
 }  // namespace tfdp

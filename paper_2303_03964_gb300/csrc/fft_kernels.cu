@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RowsFwdG
         KernelSource ks;
         ks.P = P;
         ks.bind(st, prm);
-        constexpr int kRowBlocks = P / (2 * RegGeom<LOGP>::RG);
+        constexpr int kRowBlocks = (spec_rows(P) + 2 * RegGeom<LOGP>::RG - 1) / (2 * RegGeom<LOGP>::RG);
         for (int sb = rb - data_blocks; sb < kRowBlocks; sb += spec_blocks) {
             if constexpr (Fg::seq) rows_fwd_body_seq<LOGP>(ks, P, sb, S1, P, tw, sm);
             else rows_fwd_body_ch<LOGP>(ks, c, P, sb, S1, P, tw, sm);
@@ -163,7 +163,7 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
     gs.Gs = a.Gs;
     const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
     // spectrum row blocks: about two per SM and channel, each looping over its share
-    const int spec_blocks = std::min(Rg::P / (2 * Rg::RG), 2 * 152);
+    const int spec_blocks = std::min((spec_rows(Rg::P) + 2 * Rg::RG - 1) / (2 * Rg::RG), 2 * 152);
     return launch_pdl(k_rows_fwd_r<LOGP>, Fg::ch * (blocks + spec_blocks), Rg::T * Rg::RG, Fg::smem, s, gs, blocks,
                       spec_blocks, a.T1, a.ystride, a.S1, a.tw, (const DevState*)a.st, (const DevParams*)a.prm);
 }

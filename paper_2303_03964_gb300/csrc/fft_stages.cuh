@@ -213,7 +213,7 @@ __device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int r = 0; r < 8; ++r)
-                v[c][r] = valid ? S1[((size_t)c * NH + kx) * P + t + r * T] : make_float2(0.f, 0.f);
+                v[c][r] = valid ? s1_row<P>(S1, c, kx, t + r * T) : make_float2(0.f, 0.f);
         reg_fft_forward<LOGP, 3>(v, smc, tw, t);
         const float inv = 1.0f / ((float)P * (float)P);
 #pragma unroll
@@ -399,7 +399,7 @@ __device__ __forceinline__ void cols_body_seq(int kx, const float2* __restrict__
         for (int c = 0; c < 3; ++c) {
             float2 v[1][8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[0][r] = S1[((size_t)c * NH + kx) * P + t + r * T];
+            for (int r = 0; r < 8; ++r) v[0][r] = s1_row<P>(S1, c, kx, t + r * T);
             reg_fft_forward<LOGP, 1>(v, sm + (size_t)c * P, tw, t);
             float o[8];
 #pragma unroll
