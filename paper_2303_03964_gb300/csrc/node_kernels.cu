@@ -109,12 +109,13 @@ __global__ void __launch_bounds__(kNodeThreads) k_bbox(const float2* __restrict_
 // ---------------------------------------------------------------- FFT path: grid
 // One thread: the grid of this iteration from the layout extremes (exact FP64
 // decisions), the step s_t, the spectrum key, and the bookkeeping of the iteration.
-// Lane 1 fetches s_t from the step table while lane 0 decides the grid, so the table's
-// dependent load overlaps the FP64 work.
+// The first thread of a second warp fetches s_t from the step table while thread 0
+// decides the grid: in another warp the table's dependent loads run beside the FP64 work
+// instead of taking turns with it as a divergent branch of the same warp.
 __global__ void k_grid(NodeLaunch a, int advance) {
     pdl_wait();
     pdl_trigger();
-    if (threadIdx.x == 1) {
+    if (threadIdx.x == 32) {
         a.st->step_cur = step_size(a.st->iter, *a.prm);
         return;
     }
@@ -731,7 +732,7 @@ cudaError_t launch_bbox(const NodeLaunch& a, int slot, cudaStream_t s) {
 }
 
 cudaError_t launch_fft_grid(const NodeLaunch& a, int advance, cudaStream_t s) {
-    return launch_pdl(k_grid, 1, 32, 0, s, a, advance);
+    return launch_pdl(k_grid, 1, 64, 0, s, a, advance);
 }
 
 cudaError_t launch_fft_sort(const NodeLaunch& a, cudaStream_t s) {
