@@ -60,7 +60,7 @@ WORKLOADS = {
 #       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --no-batch --no-serving
 #       --no-dynamic-k --no-quality --no-workloads --no-mixed
 NCU_TRAFFIC = {
-    ("lattice_1m", "cols"): {"bytes": 50454784 + 911360, "sha": "343b63f4cdcf4e2c"},
+    ("lattice_1m", "cols"): {"bytes": 50455296 + 1052928, "sha": "2888cc57475acbcf"},
 }
 
 # Stages timed by the library that are ONE kernel on the critical path, and that kernel
