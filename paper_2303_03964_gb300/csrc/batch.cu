@@ -50,12 +50,14 @@ __global__ void k_batch_bbox(BatchArgs a, int slot) {
     for (int item = blockIdx.x; item < n_node_items; item += gridDim.x) {
         const int g = owner(a.pre_nodes, a.B, item);
         const BGraph G = a.graphs[g];
-        const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
         float mn = INFINITY, mx = -INFINITY;
-        if (v < G.n) {
-            const float2 p = a.xy[slot][G.node_off + v];
-            mn = fminf(p.x, p.y);
-            mx = fmaxf(p.x, p.y);
+        for (int u = 0; u < kBNodesPerThread; ++u) {
+            const int v = (item - __ldg(a.pre_nodes + g)) * kBNodeChunk + u * kBThreads + threadIdx.x;
+            if (v < G.n) {
+                const float2 p = a.xy[slot][G.node_off + v];
+                mn = fminf(mn, fminf(p.x, p.y));
+                mx = fmaxf(mx, fmaxf(p.x, p.y));
+            }
         }
         mn = warp_min(mn);
         mx = warp_max(mx);
@@ -216,7 +218,7 @@ tfdp_status batch_refresh(BatchPart* b) {
         BK(cudaMemcpyAsync(&b->d_st[g].bbox[slot][0], init, sizeof(init), cudaMemcpyHostToDevice, b->stream));
     }
     BK(cudaStreamSynchronize(b->stream));
-    k_batch_bbox<<<1024, kBChunk, 0, b->stream>>>(b->args, slot);
+    k_batch_bbox<<<1024, kBThreads, 0, b->stream>>>(b->args, slot);
     BK(cudaGetLastError());
     if (b->N > 0) {
         k_batch_order_reset<<<1024, 256, 0, b->stream>>>((int)b->N, b->args.xy[slot], b->args.vxy[slot],
@@ -337,7 +339,7 @@ tfdp_status part_create(int32_t num_graphs, const int64_t* n, const int64_t* m, 
         G.Gs = (int)up((size_t)G.G_max, 4);
         G.ystride = (int)up((size_t)G.G_max, 32);
         G.nbox_max = n_int_max * n_int_max;
-        pre_nodes.push_back(pre_nodes.back() + (G.n + kBChunk - 1) / kBChunk);
+        pre_nodes.push_back(pre_nodes.back() + (G.n + kBNodeChunk - 1) / kBNodeChunk);
         pre_boxes.push_back(pre_boxes.back() + (G.nbox_max + kBChunk - 1) / kBChunk);
         pre_rows.push_back(pre_rows.back() + (G.G_max + 2 * RG - 1) / (2 * RG) + (spec_rows(b->P) + 2 * RG - 1) / (2 * RG));
         pre_cols.push_back(pre_cols.back() + (int)((NH + CG - 1) / CG));

@@ -28,7 +28,9 @@ namespace bk {
 namespace cg = cooperative_groups;
 
 constexpr int kBThreads = 256;   // threads per CTA in every phase
-constexpr int kBChunk = 256;     // nodes / boxes per work item
+constexpr int kBChunk = 256;     // boxes per work item (a thread each)
+constexpr int kBNodesPerThread = 2;                      // nodes per thread in the node phases
+constexpr int kBNodeChunk = kBThreads * kBNodesPerThread;  // nodes per work item
 
 // Per-graph geometry and buffers (device copy).
 struct BGraph {
@@ -88,45 +90,58 @@ __device__ __forceinline__ int owner(const int* __restrict__ pre, int B, int it)
 // phase 0: grid policy, step and spectrum key of graph g (one thread)
 __device__ __forceinline__ void ph_grid(const BatchArgs& a, int g) { grid_decide(a.st + g, a.prm[g], a.advance); }
 
-// phase 1: binning (visit order) and attraction (caller order) of node chunk `item`
+// phase 1: binning (visit order) and attraction (caller order) of node chunk `item`, two
+// nodes per thread (slots base and base + kBThreads, both position loads in flight)
 __device__ __forceinline__ void ph_bin(const BatchArgs& a, int item, int lane) {
     const int g = owner(a.pre_nodes, a.B, item);
     const BGraph G = a.graphs[g];
     const DevState* st = a.st + g;
     const int cur = (int)(st->t_cur & 1);
-    const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
-    if (v < G.n) {
-        const int gv = G.node_off + v;
-        const float2 p = a.vxy[cur][gv];
-        float tq;
-        const int bx = box_of(p.x, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
-        const int by = box_of(p.y, st->grid.lo_f, st->grid.h_f, st->grid.n_int, &tq);
-        const int key = by * st->grid.n_int + bx;
-        const unsigned active = __activemask();
-        const unsigned same = __match_any_sync(active, key);
-        const int leader = __ffs(same) - 1;
-        int base = 0;
-        if (lane == leader) base = atomicAdd(G.cnt + key, __popc(same));
-        base = __shfl_sync(same, base, leader);
-        a.keyslot[gv] = make_int2(key, base + __popc(same & ((1u << lane) - 1u)));
+    const int base = (item - __ldg(a.pre_nodes + g)) * kBNodeChunk + threadIdx.x;
+    const float lo = st->grid.lo_f, h = st->grid.h_f;
+    const int n_int = st->grid.n_int;
+    float2 p[kBNodesPerThread];
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int v = base + u * kBThreads;
+        p[u] = (v < G.n) ? a.vxy[cur][G.node_off + v] : make_float2(0.0f, 0.0f);
     }
-    // attraction of caller-order node gv (rowptr holds local offsets): a thread per node,
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int v = base + u * kBThreads;
+        if (v < G.n) {
+            float tq;
+            const int key = box_of(p[u].y, lo, h, n_int, &tq) * n_int + box_of(p[u].x, lo, h, n_int, &tq);
+            const unsigned active = __activemask();
+            const unsigned same = __match_any_sync(active, key);
+            const int leader = __ffs(same) - 1;
+            int b = 0;
+            if (lane == leader) b = atomicAdd(G.cnt + key, __popc(same));
+            b = __shfl_sync(same, b, leader);
+            a.keyslot[G.node_off + v] = make_int2(key, b + __popc(same & ((1u << lane) - 1u)));
+        }
+    }
+    // attraction of caller-order nodes (rowptr holds local offsets): a thread per node,
     // and the whole warp for a node of degree above kHeavyDegree, with the single-graph
     // kernel's two functions (so every node gets its solo-run sum)
     const int* rp = a.rowptr + G.rowptr_off;
     const int* cl = a.col + G.col_off;
     const float alpha = (float)a.prm[g].alpha, beta = (float)a.prm[g].beta;
-    const bool mine = v < G.n;
-    const int gv = G.node_off + (mine ? v : 0);
-    const float2 pi = a.xy[cur][gv];
-    const bool heavy = mine && rp[v + 1] - rp[v] > kHeavyDegree;
-    if (mine && !heavy) a.fatt[gv] = attraction(v, pi, rp, cl, a.xy[cur], alpha, beta, nullptr);
-    for (unsigned hm = __ballot_sync(0xffffffffu, heavy); hm; hm &= hm - 1) {
-        const int src = __ffs(hm) - 1;
-        const int hv = __shfl_sync(0xffffffffu, v, src);
-        const float2 hp = make_float2(__shfl_sync(0xffffffffu, pi.x, src), __shfl_sync(0xffffffffu, pi.y, src));
-        const float2 f = attraction_warp<false>(hv, hp, rp, cl, a.xy[cur], alpha, beta, nullptr, lane);
-        if (lane == src) a.fatt[gv] = f;
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int v = base + u * kBThreads;
+        const bool mine = v < G.n;
+        const int gv = G.node_off + (mine ? v : 0);
+        const float2 pi = a.xy[cur][gv];
+        const bool heavy = mine && rp[v + 1] - rp[v] > kHeavyDegree;
+        if (mine && !heavy) a.fatt[gv] = attraction(v, pi, rp, cl, a.xy[cur], alpha, beta, nullptr);
+        for (unsigned hm = __ballot_sync(0xffffffffu, heavy); hm; hm &= hm - 1) {
+            const int src = __ffs(hm) - 1;
+            const int hv = __shfl_sync(0xffffffffu, v, src);
+            const float2 hp = make_float2(__shfl_sync(0xffffffffu, pi.x, src), __shfl_sync(0xffffffffu, pi.y, src));
+            const float2 f = attraction_warp<false>(hv, hp, rp, cl, a.xy[cur], alpha, beta, nullptr, lane);
+            if (lane == src) a.fatt[gv] = f;
+        }
     }
 }
 
@@ -183,22 +198,35 @@ __device__ __forceinline__ void ph_scan(const BatchArgs& a, int g, int lane) {
     __syncthreads();
 }
 
-// phase 3: scatter of node chunk `item` into the new cell-sorted order
+// phase 3: scatter of node chunk `item` into the new cell-sorted order (two nodes per
+// thread, their dependent loads in flight together)
 __device__ __forceinline__ void ph_scatter(const BatchArgs& a, int item) {
     const int g = owner(a.pre_nodes, a.B, item);
     const BGraph G = a.graphs[g];
     DevState* st = a.st + g;
     const int cur = (int)(st->t_cur & 1);
-    const int v = (item - __ldg(a.pre_nodes + g)) * kBChunk + threadIdx.x;
-    if (v < G.n) {
-        const int gv = G.node_off + v;
-        const int2 ks = a.keyslot[gv];
-        const int pos = G.off[ks.x] + ks.y;
-        const int i = a.vperm[cur][gv];
+    const int base = (item - __ldg(a.pre_nodes + g)) * kBNodeChunk + threadIdx.x;
+    int2 ks[kBNodesPerThread];
+    int ii[kBNodesPerThread];
+    float2 pp[kBNodesPerThread];
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int v = base + u * kBThreads;
+        const int gv = G.node_off + (v < G.n ? v : 0);
+        ks[u] = a.keyslot[gv];
+        ii[u] = a.vperm[cur][gv];
+        pp[u] = a.vxy[cur][gv];
+    }
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int v = base + u * kBThreads;
+        if (v >= G.n) continue;
+        const int pos = G.off[ks[u].x] + ks[u].y;
+        const int i = ii[u];
         if ((unsigned)pos >= (unsigned)G.n || i < G.node_off || i >= G.node_off + G.n) {
             atomicOr(&st->flags, FLAG_SORT_RANGE);
         } else {
-            a.vxy[cur ^ 1][G.node_off + pos] = a.vxy[cur][gv];
+            a.vxy[cur ^ 1][G.node_off + pos] = pp[u];
             a.vperm[cur ^ 1][G.node_off + pos] = i;
         }
     }
@@ -273,28 +301,38 @@ __device__ __forceinline__ void ph_gather(const BatchArgs& a, int item, int lane
     const int cur = (int)(st->t_cur & 1);
     const int nxt = cur ^ 1;
     const int chunk = item - __ldg(a.pre_nodes + g);
-    const int s = chunk * kBChunk + threadIdx.x;
+    const int base = chunk * kBNodeChunk + threadIdx.x;
+    const AxisGeom ag = axis_geom(st->grid);
+    const float step = (float)st->step_cur;
     float mn = INFINITY, mx = -INFINITY, sfx = 0.0f, sfy = 0.0f;
     unsigned bad = 0;
-    if (s < G.n) {
-        const int gs = G.node_off + s;
-        const float2 p = a.vxy[nxt][gs];
-        const int i = a.vperm[nxt][gs];
-        if (i >= G.node_off && i < G.node_off + G.n) {
-            const float2 fr = gather_frep<K>(p, axis_geom(st->grid), G.gout, G.Gs);
-            sfx = fr.x;
-            sfy = fr.y;
-            if (a.eval) {
-                a.frep[i] = fr;
-            } else {
-                const float2 fa = a.fatt[i];
-                const float2 q = capped_step(p, make_float2(fr.x + fa.x, fr.y + fa.y), (float)st->step_cur);
-                if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
-                a.xy[nxt][i] = q;
-                a.vxy[nxt][gs] = q;
-                mn = fminf(q.x, q.y);
-                mx = fmaxf(q.x, q.y);
-            }
+    float2 p[kBNodesPerThread];
+    int ii[kBNodesPerThread];
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int s = base + u * kBThreads;
+        const int gs = G.node_off + (s < G.n ? s : 0);
+        p[u] = a.vxy[nxt][gs];
+        ii[u] = a.vperm[nxt][gs];
+    }
+#pragma unroll
+    for (int u = 0; u < kBNodesPerThread; ++u) {
+        const int s = base + u * kBThreads;
+        const int i = ii[u];
+        if (s >= G.n || i < G.node_off || i >= G.node_off + G.n) continue;
+        const float2 fr = gather_frep<K>(p[u], ag, G.gout, G.Gs);
+        sfx += fr.x;
+        sfy += fr.y;
+        if (a.eval) {
+            a.frep[i] = fr;
+        } else {
+            const float2 fa = a.fatt[i];
+            const float2 q = capped_step(p[u], make_float2(fr.x + fa.x, fr.y + fa.y), step);
+            if (!(isfinite(q.x) && isfinite(q.y))) bad = 1;
+            a.xy[nxt][i] = q;
+            a.vxy[nxt][G.node_off + s] = q;
+            mn = fminf(mn, fminf(q.x, q.y));
+            mx = fmaxf(mx, fmaxf(q.x, q.y));
         }
     }
     if (bad) atomicOr(&st->flags, FLAG_NONFINITE);
