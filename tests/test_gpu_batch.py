@@ -88,6 +88,24 @@ def test_batch_layout_equals_solo(tfdp, phases):
             assert _rel(out_b, out_s) <= POS_TOL, (q, _rel(out_b, out_s))
 
 
+def test_batch_launch_shapes_bitwise_equal(tfdp):
+    """One launch per phase and one cooperative launch run the same phase bodies, and every
+    sum on the path is order-independent (the spread in exact fixed point), so a layout is
+    bit for bit the same under both shapes, with a k = 1 part and a k = 3 part."""
+    graphs = _mixed_graphs(6, 55, nmin=400, nmax=4000)
+    params = [tfdp.params_default(k_interp=(1 if q % 2 else 3), grid_max=255, total_iters=40)
+              for q in range(len(graphs))]
+    outs = []
+    for phases in (True, False):
+        with tfdp.Batch(graphs, params) as b:
+            assert b.num_parts() == 2
+            b.set_phase_launches(phases)
+            b.iterate(7)
+            outs.append([b.get_positions(q) for q in range(len(graphs))])
+    for q in range(len(graphs)):
+        assert np.array_equal(outs[0][q], outs[1][q]), q
+
+
 def test_batch_parts_of_mixed_k_and_fft_size_equal_solo(tfdp):
     """Graphs with different k and grid caps run as several parts (one set of launches
     per (k, FFT size)); each graph still gives its solo run's forces and layout, and the
