@@ -50,6 +50,9 @@ cudaError_t prepare_fft(int logP);
 // (scale-free graphs have hubs whose neighbour lists a single thread would walk for
 // milliseconds).
 constexpr int kHeavyDegree = 32;
+// Target nodes per thread of the exact all-pairs kernel (a CTA owns this many times its
+// thread count); the host sizes the source chunks by the resulting CTA count.
+constexpr int kExactTargets = 2;
 
 struct NodeLaunch {
     int n;

@@ -578,11 +578,12 @@ __device__ __forceinline__ void exact_pair(unsigned long long pi2, float qx, flo
     f2 = f2_fma(f2_pack(K, K), d, f2);
 }
 
-// Tiled all-pairs repulsion: each CTA owns kNodeThreads targets and one chunk of the
-// sources (blockIdx.y), staging source tiles in shared memory. Partial sums per chunk
-// go to part[chunk][i]; k_edge_update adds them in chunk order (deterministic). A full
-// tile is read two sources per 16-byte shared load; (dx, dy) and the (fx, fy) sums use
-// the paired operations.
+// Tiled all-pairs repulsion: each CTA owns kExactTargets x kNodeThreads targets (each
+// thread kExactTargets of them, kNodeThreads apart) and one chunk of the sources
+// (blockIdx.y), staging source tiles in shared memory; every source read from shared
+// memory serves all of a thread's targets. Partial sums per chunk go to part[chunk][i];
+// k_edge_update adds them in chunk order (deterministic). A full tile is read two sources
+// per 16-byte shared load; (dx, dy) and the (fx, fy) sums use the paired operations.
 template <int GI, bool W>
 __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advance) {
     pdl_wait();
@@ -604,16 +605,23 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
     const float gamma = (float)a.prm->gamma;
     __shared__ __align__(16) float2 tile[kNodeThreads];
     __shared__ __align__(8) float tile_w[W ? kNodeThreads : 2];  // source weights r_j (local refinement)
-    const int i = blockIdx.x * kNodeThreads + threadIdx.x;
-    const float2 pi = (i < a.n) ? xy[i] : make_float2(0.f, 0.f);
-    const unsigned long long pi2 = f2_pack(pi.x, pi.y);
+    int ii[kExactTargets];
+    unsigned long long pi2[kExactTargets], f2[kExactTargets];
+    float2 pi0 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < kExactTargets; ++q) {
+        ii[q] = blockIdx.x * (kExactTargets * kNodeThreads) + q * kNodeThreads + threadIdx.x;
+        const float2 pi = (ii[q] < a.n) ? xy[ii[q]] : make_float2(0.f, 0.f);
+        if (q == 0) pi0 = pi;
+        pi2[q] = f2_pack(pi.x, pi.y);
+        f2[q] = f2_pack(0.0f, 0.0f);
+    }
     const int csize = (a.n + a.nchunks - 1) / a.nchunks;
     const int j0 = blockIdx.y * csize;
     const int j1 = min(a.n, j0 + csize);
-    unsigned long long f2 = f2_pack(0.0f, 0.0f);
     for (int s0 = j0; s0 < j1; s0 += kNodeThreads) {
         const int j = s0 + threadIdx.x;
-        tile[threadIdx.x] = (j < j1) ? xy[j] : pi;
+        tile[threadIdx.x] = (j < j1) ? xy[j] : pi0;
         if (W) tile_w[threadIdx.x] = (j < j1) ? a.wrep[j] : 0.0f;
         __syncthreads();
         const int cnt = min(kNodeThreads, j1 - s0);
@@ -622,22 +630,30 @@ __global__ void __launch_bounds__(kNodeThreads) k_exact(NodeLaunch a, int advanc
             const float2* w2 = reinterpret_cast<const float2*>(tile_w);
 #pragma unroll 4
             for (int jj = 0; jj < kNodeThreads / 2; ++jj) {
-                const float4 q = t4[jj];  // sources 2 jj and 2 jj + 1, in that order
+                const float4 q4 = t4[jj];  // sources 2 jj and 2 jj + 1, in that order
                 const float2 wq = W ? w2[jj] : make_float2(1.0f, 1.0f);
-                exact_pair<GI, W>(pi2, q.x, q.y, wq.x, gamma, f2);
-                exact_pair<GI, W>(pi2, q.z, q.w, wq.y, gamma, f2);
+#pragma unroll
+                for (int q = 0; q < kExactTargets; ++q) {
+                    exact_pair<GI, W>(pi2[q], q4.x, q4.y, wq.x, gamma, f2[q]);
+                    exact_pair<GI, W>(pi2[q], q4.z, q4.w, wq.y, gamma, f2[q]);
+                }
             }
         } else {
             for (int jj = 0; jj < cnt; ++jj) {
-                const float2 q = tile[jj];
-                exact_pair<GI, W>(pi2, q.x, q.y, W ? tile_w[jj] : 1.0f, gamma, f2);
+                const float2 q2 = tile[jj];
+#pragma unroll
+                for (int q = 0; q < kExactTargets; ++q)
+                    exact_pair<GI, W>(pi2[q], q2.x, q2.y, W ? tile_w[jj] : 1.0f, gamma, f2[q]);
             }
         }
         __syncthreads();
     }
-    float fx, fy;
-    f2_unpack(f2, fx, fy);
-    if (i < a.n) a.part[(size_t)blockIdx.y * a.n + i] = make_float2(fx, fy);
+#pragma unroll
+    for (int q = 0; q < kExactTargets; ++q) {
+        float fx, fy;
+        f2_unpack(f2[q], fx, fy);
+        if (ii[q] < a.n) a.part[(size_t)blockIdx.y * a.n + ii[q]] = make_float2(fx, fy);
+    }
 }
 
 // Attraction + update in caller order, on the repulsion summed over `nchunks` partial
@@ -796,7 +812,7 @@ cudaError_t launch_fft_back(const NodeLaunch& a, int advance, int eval, cudaStre
 }
 
 cudaError_t launch_exact_pairs(const NodeLaunch& a, int advance, cudaStream_t s) {
-    dim3 grid(blocks_for(a.n, kNodeThreads), a.nchunks);
+    dim3 grid(blocks_for(a.n, kExactTargets * kNodeThreads), a.nchunks);
     switch (a.gamma_int) {
         case 2: return launch_pdl(a.wrep ? k_exact<2, true> : k_exact<2, false>, grid, kNodeThreads, 0, s, a, advance);
         case 4: return launch_pdl(a.wrep ? k_exact<4, true> : k_exact<4, false>, grid, kNodeThreads, 0, s, a, advance);

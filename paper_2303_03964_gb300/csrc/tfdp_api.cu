@@ -218,14 +218,16 @@ struct tfdp_graph {
 
 namespace {
 
-// Source chunks of the exact path for nb target CTAs: at least about four CTAs per SM in
-// total (nb * chunks >= 4 * 152), and among the next few counts the one whose CTAs
-// divide most evenly over the 152 SMs (every CTA does the same work).
-int exact_chunks(int nb) {
-    const int c0 = std::max(1, std::min(nb, (4 * 152 + nb - 1) / nb));
+// Source chunks of the exact path for nb target CTAs and n nodes: at least about four
+// CTAs per SM in total (nb * chunks >= 4 * 152) while every chunk keeps at least 64
+// sources, and among the next few counts the one whose CTAs divide most evenly over the
+// 152 SMs (every CTA does the same work).
+int exact_chunks(int nb, int64_t n) {
+    const int cmax = (int)std::max<int64_t>(1, std::min<int64_t>(1 << 16, (n + 63) / 64));
+    const int c0 = std::max(1, std::min(cmax, (4 * 152 + nb - 1) / nb));
     int best = c0;
     double best_imb = 1e30;
-    for (int c = c0; c <= std::min(nb, c0 + 8); ++c) {
+    for (int c = c0; c <= std::min(cmax, c0 + 8); ++c) {
         const double per_sm = (double)nb * c / 152.0;
         const double imb = std::ceil(per_sm) / per_sm;
         if (imb < best_imb - 1e-9) {
@@ -778,8 +780,8 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     }
 
     // exact-path chunking
-    const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
-    g->nchunks = exact_chunks(nb);
+    const int nb = (int)std::max<int64_t>(1, (n + 256 * kExactTargets - 1) / (256 * kExactTargets));
+    g->nchunks = exact_chunks(nb, n);
 
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     Arena A;
@@ -1123,8 +1125,8 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
     tfdp_status st = tfdp_params_check(&p, nullptr);
     if (st != TFDP_OK) return st;
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
-    const int nb = (int)std::max<int64_t>(1, (n + 255) / 256);
-    const int nchunks = exact_chunks(nb);
+    const int nb = (int)std::max<int64_t>(1, (n + 256 * kExactTargets - 1) / (256 * kExactTargets));
+    const int nchunks = exact_chunks(nb, n);
     size_t b = 0;
     b += sizeof(float2) * nn * (4 + (size_t)nchunks) + sizeof(int) * (nn + 1) + sizeof(int) * (size_t)(2 * m);
     b += sizeof(int) * (size_t)std::min<int64_t>((int64_t)nn, 2 * m / (kHeavyDegree + 1) + 1);  // hub list bound
