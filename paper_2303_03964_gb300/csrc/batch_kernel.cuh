@@ -7,9 +7,8 @@
 // distributing (graph, item) work over CTAs. Two launch shapes run them: one cooperative
 // persistent launch for `iters` iterations with a grid-wide barrier between phases, or
 // nine ordinary launches per iteration, one CTA per item (the launch-shape autotuner
-// keeps the faster). The
-// per-node and per-transform arithmetic is the single-graph code (node_dev.cuh,
-// fft_stages.cuh), so every graph evolves as it would alone.
+// keeps the faster). The per-node and per-transform arithmetic is the single-graph code
+// (node_dev.cuh, fft_stages.cuh), so every graph evolves as it would alone.
 #pragma once
 
 #include <cooperative_groups.h>
