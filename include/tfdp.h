@@ -54,7 +54,16 @@ typedef enum {
 /* How the repulsive sum is evaluated. */
 typedef enum {
     TFDP_REP_EXACT = 0, /* tiled all-pairs sum of Eq. (repfK), Sec. 3.4 "exact method" */
-    TFDP_REP_FFT = 1    /* interpolation-based FFT of Sec. 3.4 */
+    TFDP_REP_FFT = 1,   /* interpolation-based FFT of Sec. 3.4 */
+    TFDP_REP_AUTO = 2   /* whichever of the two has the shorter estimated iteration for the
+                         * graph's n (Sec. 4.1 "Runtime Performance" finds the exact method
+                         * faster than ibFFT below about 500 nodes on its hardware):
+                         * the exact sum while 9 us + n^2 / 3.0e12 s <= 40 us + 15 us per doubling
+                         * of the FFT size P above 512 (measured on GB300: the exact sum up to
+                         * n ~ 9,600 at P = 512 and ~13,500 at P = 2048). Resolved when the graph
+                         * is created and at each tfdp_set_params; tfdp_get_params reports the
+                         * resolved mode, tfdp_graph_footprint sizes for it. tfdp_params_check
+                         * checks AUTO parameters as for TFDP_REP_FFT. */
 } tfdp_rep_mode;
 
 /* Arithmetic of the grid convolution (the FFT step of Sec. 3.4). */
@@ -90,7 +99,7 @@ typedef struct {
     int32_t n_int_min;   /* lower bound of N_int, default 50 (Sec. 3.4) */
     int32_t grid_max;    /* cap on G = N_int * k, default 1023; sizes the FFT: P = nextpow2(2 grid_max - 1) */
     int32_t grid_policy; /* tfdp_grid_policy, default TFDP_GRID_SNAP_H */
-    int32_t rep_mode;    /* tfdp_rep_mode, default TFDP_REP_FFT */
+    int32_t rep_mode;    /* tfdp_rep_mode, default TFDP_REP_FFT (a graph holds EXACT or FFT) */
     int32_t precision;   /* tfdp_precision, default TFDP_PREC_FP32 */
     double step0;        /* s0, default 1.0 (layout units) */
     double step_min;     /* s_min, default 0.01 */

@@ -677,6 +677,22 @@ const char* tfdp_status_str(tfdp_status s) {
 
 const char* tfdp_last_cuda_error(void) { return g_cuda_err.c_str(); }
 
+// TFDP_REP_AUTO -> the mode with the shorter estimated iteration for a graph of n nodes.
+// Measured on GB300 (Erdos-Renyi graphs of mean degree 8, n = 500 ... 48,000, FFT sizes
+// P = 512 and 2048): an exact iteration takes about 9 us + n^2 / 3.0e12 pairs/s; an FFT
+// iteration about 40 us at P <= 512 plus 15 us per doubling of P above 512, nearly
+// independent of n at these sizes (its kernel chain, not its work, sets the time). The
+// crossover falls near n = 9,600 at P = 512 and 13,500 at P = 2048 (measured: between
+// 8,000 and 12,000, and near 16,000).
+int resolve_rep_mode(const tfdp_params& p, int64_t n) {
+    if (p.rep_mode != TFDP_REP_AUTO) return p.rep_mode;
+    int P, logP, G, nb;
+    if (!fft_geometry(p, &P, &logP, &G, &nb)) return TFDP_REP_EXACT;
+    const double t_fft = 40e-6 + 15e-6 * (double)std::max(0, logP - 9);
+    const double t_exact = 9e-6 + (double)n * (double)n / 3.0e12;
+    return t_exact <= t_fft ? TFDP_REP_EXACT : TFDP_REP_FFT;
+}
+
 tfdp_status tfdp_params_default(tfdp_params* out) {
     if (!out) return TFDP_ERR_INVALID_ARG;
     std::memset(out, 0, sizeof(*out));
@@ -704,13 +720,14 @@ tfdp_status tfdp_params_check(const tfdp_params* p, int* weight_ok) {
     if (p->n_int_min < 1) return TFDP_ERR_PARAM_RANGE;
     if (p->grid_max < (p->k_interp ? p->k_interp : kMaxK)) return TFDP_ERR_PARAM_RANGE;
     if (p->grid_policy != TFDP_GRID_PAPER && p->grid_policy != TFDP_GRID_SNAP_H) return TFDP_ERR_INVALID_ARG;
-    if (p->rep_mode != TFDP_REP_EXACT && p->rep_mode != TFDP_REP_FFT) return TFDP_ERR_INVALID_ARG;
+    if (p->rep_mode != TFDP_REP_EXACT && p->rep_mode != TFDP_REP_FFT && p->rep_mode != TFDP_REP_AUTO)
+        return TFDP_ERR_INVALID_ARG;
     if (p->precision != TFDP_PREC_FP32 && p->precision != TFDP_PREC_BF16X3) return TFDP_ERR_INVALID_ARG;
     if (!(p->step_min > 0.0) || !(p->step0 >= p->step_min) || !std::isfinite(p->step0)) return TFDP_ERR_PARAM_RANGE;
     if (p->total_iters < 1) return TFDP_ERR_PARAM_RANGE;
     for (int i = 0; i < 7; ++i)
         if (p->reserved[i] != 0) return TFDP_ERR_INVALID_ARG;
-    if (p->rep_mode == TFDP_REP_FFT) {
+    if (p->rep_mode != TFDP_REP_EXACT) {  // FFT, or AUTO, which may resolve to FFT
         int P, l, G, nb;
         if (!fft_geometry(*p, &P, &l, &G, &nb)) return TFDP_ERR_PARAM_RANGE;
         if ((nb + scan_items_per_block() - 1) / scan_items_per_block() > 1024) return TFDP_ERR_PARAM_RANGE;
@@ -731,6 +748,7 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     else tfdp_params_default(&p);
     tfdp_status st = tfdp_params_check(&p, nullptr);
     if (st != TFDP_OK) return st;
+    p.rep_mode = resolve_rep_mode(p, n);
 
     // validate edges and build the symmetric CSR (rows sorted by neighbour id)
     std::vector<int64_t> keys((size_t)m);
@@ -856,10 +874,13 @@ tfdp_status tfdp_create_graph(int64_t n, int64_t m, const int32_t* edges, const 
     return TFDP_OK;
 }
 
-tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* p) {
-    if (!g || !p) return TFDP_ERR_INVALID_ARG;
-    tfdp_status st = tfdp_params_check(p, nullptr);
+tfdp_status tfdp_set_params(tfdp_graph* g, const tfdp_params* given) {
+    if (!g || !given) return TFDP_ERR_INVALID_ARG;
+    tfdp_status st = tfdp_params_check(given, nullptr);
     if (st != TFDP_OK) return st;
+    tfdp_params resolved = *given;
+    resolved.rep_mode = resolve_rep_mode(resolved, g->n);
+    const tfdp_params* p = &resolved;
     const bool to_fft = p->rep_mode == TFDP_REP_FFT && g->params.rep_mode != TFDP_REP_FFT;
     const bool prec_changed = p->precision != g->params.precision;
     g->params = *p;
@@ -1124,6 +1145,7 @@ tfdp_status tfdp_graph_footprint(int64_t n, int64_t m, const tfdp_params* params
     else tfdp_params_default(&p);
     tfdp_status st = tfdp_params_check(&p, nullptr);
     if (st != TFDP_OK) return st;
+    p.rep_mode = resolve_rep_mode(p, n);
     const size_t nn = (size_t)std::max<int64_t>(n, 1);
     const int nb = (int)std::max<int64_t>(1, (n + 256 * kExactTargets - 1) / (256 * kExactTargets));
     const int nchunks = exact_chunks(nb, n);

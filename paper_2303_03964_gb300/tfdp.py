@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libtfdp.so")
 
-REP_EXACT, REP_FFT = 0, 1
+REP_EXACT, REP_FFT, REP_AUTO = 0, 1, 2  # REP_AUTO: resolved by n at creation / set_params
 PREC_FP32, PREC_BF16X3 = 0, 1
 GRID_PAPER, GRID_SNAP_H = 0, 1
 K_DYNAMIC = 0  # k_interp: the dynamic k schedule (1, then 2, then 3)

@@ -121,3 +121,29 @@ def test_bf16x3_precision_mode_accepted_only_at_its_fft_size():
     # the exact path has no grid convolution: the mode is accepted and changes nothing
     assert tfdp.params_check(tfdp.params_default(precision=tfdp.PREC_BF16X3, rep_mode=tfdp.REP_EXACT,
                                                  grid_max=255)) is True
+
+
+@pytest.mark.parametrize("grid_max,n_exact,n_fft", [(255, 9000, 10000), (1023, 13000, 14000)])
+def test_auto_mode_resolves_by_graph_size(grid_max, n_exact, n_fft):
+    # AUTO takes the exact sum while its estimated iteration (9 us + n^2 / 3e12 s) is no
+    # longer than the FFT path's (40 us at P <= 512, + 15 us per doubling of P); the
+    # footprint is sized for the resolved mode
+    auto = tfdp.params_default(rep_mode=tfdp.REP_AUTO, grid_max=grid_max)
+    assert tfdp.params_check(auto) is True
+    for n, want in ((n_exact, tfdp.REP_EXACT), (n_fft, tfdp.REP_FFT)):
+        other = tfdp.REP_FFT if want == tfdp.REP_EXACT else tfdp.REP_EXACT
+        fp = tfdp.graph_footprint(n, 4 * n, auto)
+        assert fp == tfdp.graph_footprint(n, 4 * n, tfdp.params_default(rep_mode=want, grid_max=grid_max))
+        assert fp != tfdp.graph_footprint(n, 4 * n, tfdp.params_default(rep_mode=other, grid_max=grid_max))
+
+
+def test_auto_mode_is_checked_as_fft():
+    # AUTO may resolve to the FFT path, so its FFT-only limits apply
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.params_check(tfdp.params_default(rep_mode=tfdp.REP_AUTO, precision=tfdp.PREC_BF16X3, grid_max=255))
+    assert ei.value.status == 3
+    assert tfdp.params_check(tfdp.params_default(rep_mode=tfdp.REP_AUTO, precision=tfdp.PREC_BF16X3,
+                                                 grid_max=1023)) is True
+    with pytest.raises(tfdp.TfdpError) as ei:
+        tfdp.params_check(tfdp.params_default(rep_mode=3))
+    assert ei.value.status == 1

@@ -299,6 +299,34 @@ def test_fft_sort_and_spread_units(tfdp):
     assert record("spread_mx_err_over_h_rho", float(err_m)) < 1e-5
 
 
+def test_auto_mode_runs_the_resolved_path(tfdp):
+    """TFDP_REP_AUTO resolves by n at creation and at set_params (exact for 2,000 nodes,
+    FFT for 20,000 at grid cap 255) and then runs exactly that path: bit-identical
+    layouts to the explicitly chosen mode."""
+    rng = np.random.default_rng(77)
+    graphs = {}
+    for n, want in ((2000, tfdp.REP_EXACT), (20000, tfdp.REP_FFT)):
+        e = synth.erdos_renyi(n, 4 * n, rng)
+        xy = rng.uniform(-50, 50, size=(n, 2)).astype(np.float32)
+        graphs[n] = (e, xy)
+        outs = []
+        for mode in (tfdp.REP_AUTO, want):
+            with tfdp.Graph(n, e, xy, _params(tfdp, rep_mode=mode, grid_max=255)) as g:
+                assert g.get_params().rep_mode == want
+                g.iterate(5)
+                outs.append(g.get_positions())
+                assert g.stats()["kernels_per_iteration"] == (2 if want == tfdp.REP_EXACT else 10)
+        assert np.array_equal(outs[0], outs[1])
+    e, xy = graphs[2000]
+    with tfdp.Graph(2000, e, xy, _params(tfdp, rep_mode=tfdp.REP_FFT, grid_max=255)) as g:
+        g.iterate(2)
+        g.set_params(_params(tfdp, rep_mode=tfdp.REP_AUTO, grid_max=255))
+        assert g.get_params().rep_mode == tfdp.REP_EXACT
+        g.iterate(2)
+        assert g.stats()["kernels_per_iteration"] == 2
+        assert np.all(np.isfinite(g.get_positions()))
+
+
 def test_fft_short_layout_matches_oracle(tfdp):
     rng = np.random.default_rng(12)
     n = 20000
