@@ -35,6 +35,9 @@
 
 namespace tfdp {
 
+constexpr int kRowsFwdPairs = 2;      // row pairs per thread in the forward row pass at P = 2048
+constexpr int kRowsFwdMinBlocks = 4;  // its CTAs per SM then (64 registers)
+
 // Row passes that keep one channel in registers at a time (the *_seq bodies): P = 8192,
 // whose sequence fills a CTA. (At P = 2048 the same bodies at four CTAs per SM, one wave
 // for the 512 row pairs of a 1023-row grid, measured 4 % slower than three channels at
@@ -52,9 +55,13 @@ template <int LOGP>
 struct RowsFwdGeom {
     static constexpr bool seq = SeqRows<LOGP>::value;
     static constexpr int ch = seq ? 1 : 3;  // CTAs per row block
+    // row pairs a thread transforms in turn: 2 at P = 2048 (T = 256, one pair per CTA
+    // otherwise), so that every block writes 32-byte runs of its output columns
+    static constexpr int rp = (!seq && RegGeom<LOGP>::T == 256) ? kRowsFwdPairs : 1;
+    static constexpr int rows = 2 * RegGeom<LOGP>::RG * (seq ? 1 : rp);  // rows per block
     static constexpr size_t smem =
-        seq ? RegGeom<LOGP>::rows_smem : (size_t)RegGeom<LOGP>::RG * RegGeom<LOGP>::P * sizeof(float2);
-    static constexpr int min_blocks = seq ? 1 : 5;
+        seq ? RegGeom<LOGP>::rows_smem : (size_t)RegGeom<LOGP>::RG * rp * RegGeom<LOGP>::P * sizeof(float2);
+    static constexpr int min_blocks = seq ? 1 : (rp > 1 ? kRowsFwdMinBlocks : 5);
 };
 
 // Blocks [0, ch data_blocks): channel b % ch of row block b / ch of the spread grid into
@@ -75,16 +82,16 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, RowsFwdG
     const int c = (int)blockIdx.x - rb * Fg::ch;
     if (rb < data_blocks) {
         if constexpr (Fg::seq) rows_fwd_body_seq<LOGP>(gsrc, st->grid.G, rb, T1, ystride, tw, sm);
-        else rows_fwd_body_ch<LOGP>(gsrc, c, st->grid.G, rb, T1, ystride, tw, sm);
+        else rows_fwd_body_ch<LOGP, GridSource, Fg::rp>(gsrc, c, st->grid.G, rb, T1, ystride, tw, sm);
     } else {
         if (st->spec_dirty == 0) return;
         KernelSource ks;
         ks.P = P;
         ks.bind(st, prm);
-        constexpr int kRowBlocks = (spec_rows(P) + 2 * RegGeom<LOGP>::RG - 1) / (2 * RegGeom<LOGP>::RG);
+        constexpr int kRowBlocks = (spec_rows(P) + Fg::rows - 1) / Fg::rows;
         for (int sb = rb - data_blocks; sb < kRowBlocks; sb += spec_blocks) {
             if constexpr (Fg::seq) rows_fwd_body_seq<LOGP>(ks, P, sb, S1, P, tw, sm);
-            else rows_fwd_body_ch<LOGP>(ks, c, P, sb, S1, P, tw, sm);
+            else rows_fwd_body_ch<LOGP, KernelSource, Fg::rp>(ks, c, P, sb, S1, P, tw, sm);
             __syncthreads();  // the next row block's exchanges reuse sm
         }
     }
@@ -161,9 +168,9 @@ static cudaError_t launch_rows_fwd_impl(const FftLaunch& a, cudaStream_t s) {
     GridSource gs;
     gs.gin = a.gin;
     gs.Gs = a.Gs;
-    const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
+    const int blocks = (a.G_max + Fg::rows - 1) / Fg::rows;
     // spectrum row blocks: about two per SM and channel, each looping over its share
-    const int spec_blocks = std::min((spec_rows(Rg::P) + 2 * Rg::RG - 1) / (2 * Rg::RG), 2 * 152);
+    const int spec_blocks = std::min((spec_rows(Rg::P) + Fg::rows - 1) / Fg::rows, 2 * 152);
     return launch_pdl(k_rows_fwd_r<LOGP>, Fg::ch * (blocks + spec_blocks), Rg::T * Rg::RG, Fg::smem, s, gs, blocks,
                       spec_blocks, a.T1, a.ystride, a.S1, a.tw, (const DevState*)a.st, (const DevParams*)a.prm);
 }

@@ -148,40 +148,64 @@ __device__ __forceinline__ void rows_fwd_body(const Src& src, int nrows, int blk
     }
 }
 
-// Channel c only of row block `blk` (2 RG rows): the same transform and split as
+// One 32-byte global store (a 256-bit access, sm_100 and later) of a then b; p must be
+// 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(float2* p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(__cvta_generic_to_global(p)),
+                 "f"(a.x), "f"(a.y), "f"(a.z), "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+
+// Channel c only of row block `blk` (2 RG RP rows): the same transform and split as
 // rows_fwd_body computes for that channel, for launches with one CTA per (row block,
-// channel); sm holds RG sequences of P values.
-template <int LOGP, class Src>
+// channel); sm holds RG RP sequences of P values. Each thread transforms RP row pairs in
+// turn, so that the split pass writes 4 RG RP consecutive
+// floats of a column: with RG RP even, as 32-byte stores (half the store instructions of
+// 16-byte ones for the strided column-major output).
+template <int LOGP, class Src, int RP = 1>
 __device__ __forceinline__ void rows_fwd_body_ch(const Src& src, int c, int nrows, int blk, float2* __restrict__ out,
                                                  int ystride, const float2* __restrict__ tw, float2* sm) {
     using Gm = RegGeom<LOGP>;
     constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
+    constexpr int RB = RG * RP;  // row pairs of the block; pair q is rows ybase + 2q, + 1
     const int G = nrows;
-    const int ybase = blk * (2 * RG);
+    const int ybase = blk * (2 * RB);
     if (ybase >= G) return;
     const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
-    const int y0 = ybase + 2 * lr;
-    float2* smr = sm + (size_t)lr * P;
-    float2 v[1][8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int x = t + r * T;
-        v[0][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+    for (int h = 0; h < RP; ++h) {
+        const int y0 = ybase + 2 * (h * RG + lr);
+        float2 v[1][8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int x = t + r * T;
+            v[0][r] = make_float2(src(c, y0, x, G), src(c, y0 + 1, x, G));
+        }
+        float2* smr = sm + (size_t)(h * RG + lr) * P;
+        reg_fft_forward<LOGP, 1>(v, smr, tw, t);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) smr[swz(8 * t + r)] = v[0][r];
     }
-    reg_fft_forward<LOGP, 1>(v, smr, tw, t);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) smr[swz(8 * t + r)] = v[0][r];
     __syncthreads();
     for (int idx = threadIdx.x; idx < NH; idx += blockDim.x) {
         const int kx = split_freq<LOGP>(idx);
         const int pk = swz(pos_of_freq<LOGP>(kx));
         const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
-        float4* dst = reinterpret_cast<float4*>(out + ((size_t)c * NH + kx) * ystride + ybase);
+        float2* dst = out + ((size_t)c * NH + kx) * ystride + ybase;
+        float4 z[RB];
 #pragma unroll
-        for (int q = 0; q < RG; ++q) {
+        for (int q = 0; q < RB; ++q) {
             const float2* seq = sm + (size_t)q * P;
             const float2 Z = seq[pk], W = seq[pn];
-            dst[q] = make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+            z[q] = make_float4(0.5f * (Z.x + W.x), 0.5f * (Z.y - W.y), 0.5f * (Z.y + W.y), 0.5f * (W.x - Z.x));
+        }
+        if constexpr (RB % 2 == 0) {
+            // ystride is a multiple of 32 and ybase of 4: dst + 2q (q even) is 32-byte aligned
+#pragma unroll
+            for (int q = 0; q < RB; q += 2) st_global_v8(dst + 2 * q, z[q], z[q + 1]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < RB; ++q) reinterpret_cast<float4*>(dst)[q] = z[q];
         }
     }
 }
