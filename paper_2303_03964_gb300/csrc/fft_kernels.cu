@@ -37,6 +37,7 @@ namespace tfdp {
 
 constexpr int kRowsFwdPairs = 2;      // row pairs per thread in the forward row pass at P = 2048
 constexpr int kRowsFwdMinBlocks = 4;  // its CTAs per SM then (64 registers)
+constexpr int kRowsInvPairs = 2;      // row pairs per thread in the inverse row pass at P = 2048
 
 // Row passes that keep one channel in registers at a time (the *_seq bodies): P = 8192,
 // whose sequence fills a CTA. (At P = 2048 the same bodies at four CTAs per SM, one wave
@@ -112,6 +113,15 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::CG, RegGeom<
         cols_body<LOGP>(blockIdx.x, T1, T2, ystride, specK, specHx, specHy, S1, tw, st->grid.G, st->spec_dirty, sm);
 }
 
+// Inverse row pass: two row pairs per thread at P = 2048 (as the forward pass), read as
+// 32-byte runs of their half-spectrum columns.
+template <int LOGP>
+struct RowsInvGeom {
+    static constexpr int rp = (!SeqRows<LOGP>::value && RegGeom<LOGP>::T == 256) ? kRowsInvPairs : 1;
+    static constexpr int rows = 2 * RegGeom<LOGP>::RG * rp;  // rows per block
+    static constexpr size_t smem = RegGeom<LOGP>::rows_smem * rp;
+};
+
 template <int LOGP>
 __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, SeqRows<LOGP>::min_blocks)
     k_rows_inv_r(const float2* __restrict__ T2, int ystride, float4* __restrict__ gout, int Gs,
@@ -120,7 +130,7 @@ __global__ void __launch_bounds__(RegGeom<LOGP>::T * RegGeom<LOGP>::RG, SeqRows<
     pdl_wait();
     pdl_trigger();
     if constexpr (SeqRows<LOGP>::value) rows_inv_body_seq<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
-    else rows_inv_body<LOGP>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
+    else rows_inv_body<LOGP, RowsInvGeom<LOGP>::rp>(blockIdx.x, T2, ystride, gout, Gs, tw, st->grid.G, sm);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -131,7 +141,7 @@ static cudaError_t set_attrs() {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if ((e = cudaFuncSetAttribute(k_rows_fwd_r<LOGP>, A, (int)RowsFwdGeom<LOGP>::smem)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(k_cols_r<LOGP>, A, (int)Rg::cols_smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_rows_inv_r<LOGP>, A, (int)Rg::rows_smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_rows_inv_r<LOGP>, A, (int)RowsInvGeom<LOGP>::smem)) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -190,8 +200,9 @@ static cudaError_t launch_rows_inv_impl(const FftLaunch& a, cudaStream_t s) {
     using Rg = RegGeom<LOGP>;
     cudaError_t e = ensure_attrs<LOGP>();
     if (e != cudaSuccess) return e;
-    const int blocks = (a.G_max + 2 * Rg::RG - 1) / (2 * Rg::RG);
-    return launch_pdl(k_rows_inv_r<LOGP>, blocks, Rg::T * Rg::RG, Rg::rows_smem, s, (const float2*)a.T2, a.ystride,
+    using Ig = RowsInvGeom<LOGP>;
+    const int blocks = (a.G_max + Ig::rows - 1) / Ig::rows;
+    return launch_pdl(k_rows_inv_r<LOGP>, blocks, Rg::T * Rg::RG, Ig::smem, s, (const float2*)a.T2, a.ystride,
                       a.gout, a.Gs, (const float2*)a.tw, (const DevState*)a.st);
 }
 

@@ -303,28 +303,56 @@ __device__ __forceinline__ void cols_body(int cblk, const float2* __restrict__ T
 
 // Row block blk (RG row pairs): complex-to-real along x of the three outputs from T2,
 // two real rows per complex transform, written as (A, O^x, O^y, 0) for x, y < G.
-template <int LOGP>
+// One 32-byte global load (a 256-bit access, sm_100 and later) into a then b; p must be
+// 32-byte aligned.
+__device__ __forceinline__ void ld_global_v8(const float2* p, float4& a, float4& b) {
+    asm volatile("ld.global.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(__cvta_generic_to_global(p)));
+}
+
+// Inverse row transforms of row block `blk` (2 RG RP rows x 3 channels) from T2 into gout.
+// The half spectra of the block's RG RP row pairs are gathered into shared memory first
+// (with RG RP even, 32 bytes per column and load); each thread then transforms RP row
+// pairs in turn.
+template <int LOGP, int RP = 1>
 __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict__ T2, int ystride,
                                               float4* __restrict__ gout, int Gs, const float2* __restrict__ tw,
                                               int G, float2* sm) {
     using Gm = RegGeom<LOGP>;
     constexpr int P = Gm::P, T = Gm::T, RG = Gm::RG, NH = P / 2 + 1;
-    const int ybase = blk * (2 * RG);
+    constexpr int RB = RG * RP;  // row pairs of the block; pair q is rows ybase + 2q, + 1
+    const int ybase = blk * (2 * RB);
     if (ybase >= G) return;
     // Z_k = A_k + i B_k for two real rows (A, B) at row pair q, both halves of the spectrum.
     // NB items per thread and round: all their loads are in flight before the first store
-    constexpr int NB = (RG >= 4) ? 1 : 4 / RG;
+    constexpr int NB = (RB >= 4) ? 1 : 4 / RB;
     for (int i0 = threadIdx.x; i0 < 3 * NH; i0 += NB * blockDim.x) {
-        float4 X[NB][RG];
+        float4 X[NB][RB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             const int idx = i0 + b * blockDim.x;
             const int c = idx / NH;
             const int kx = split_freq<LOGP>(idx - c * NH);
-            const float4* src = reinterpret_cast<const float4*>(T2 + ((size_t)c * NH + kx) * ystride + ybase);
+            const float2* src = T2 + ((size_t)c * NH + kx) * ystride + ybase;
+            if constexpr (RB % 2 == 0) {
+                // ystride is a multiple of 32 and ybase of 4: src + 2q (q even) is 32-byte aligned;
+                // rows up to ybase + 2 RB - 1 < ystride lie inside the column
 #pragma unroll
-            for (int q = 0; q < RG; ++q)
-                X[b][q] = (idx < 3 * NH && ybase + 2 * q < G) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < RB; q += 2) {
+                    if (idx < 3 * NH && ybase + 2 * q < G) {
+                        ld_global_v8(src + 2 * q, X[b][q], X[b][q + 1]);
+                    } else {
+                        X[b][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        X[b][q + 1] = X[b][q];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RB; ++q)
+                    X[b][q] = (idx < 3 * NH && ybase + 2 * q < G) ? reinterpret_cast<const float4*>(src)[q]
+                                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
@@ -335,9 +363,10 @@ __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict_
             const int pk = swz(pos_of_freq<LOGP>(kx));
             const int pn = swz(pos_of_freq<LOGP>((P - kx) & (P - 1)));
 #pragma unroll
-            for (int q = 0; q < RG; ++q) {
+            for (int q = 0; q < RB; ++q) {
                 float4 x = X[b][q];
-                if (ybase + 2 * q + 1 >= G) { x.z = 0.f; x.w = 0.f; }  // row past G: never written
+                if (ybase + 2 * q >= G) x = make_float4(0.f, 0.f, 0.f, 0.f);  // rows past G: never written
+                if (ybase + 2 * q + 1 >= G) { x.z = 0.f; x.w = 0.f; }
                 float2* seq = sm + ((size_t)q * 3 + c) * P;
                 seq[pk] = make_float2(x.x - x.w, x.y + x.z);
                 if (kx != 0 && kx != P / 2) seq[pn] = make_float2(x.x + x.w, x.z - x.y);
@@ -346,20 +375,24 @@ __device__ __forceinline__ void rows_inv_body(int blk, const float2* __restrict_
     }
     __syncthreads();
     const int lr = threadIdx.x / T, t = threadIdx.x - lr * T;
-    const int y0 = ybase + 2 * lr;
-    float2* smr = sm + (size_t)lr * 3 * P;
-    float2 v[3][8];
+#pragma unroll 1
+    for (int h = 0; h < RP; ++h) {
+        const int pq = h * RG + lr;
+        const int y0 = ybase + 2 * pq;
+        float2* smr = sm + (size_t)pq * 3 * P;
+        float2 v[3][8];
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int r = 0; r < 8; ++r) v[c][r] = smr[c * P + swz(8 * t + r)];
-    reg_fft_inverse<LOGP, 3>(v, smr, tw, t);
+            for (int r = 0; r < 8; ++r) v[c][r] = smr[c * P + swz(8 * t + r)];
+        reg_fft_inverse<LOGP, 3>(v, smr, tw, t);
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int x = t + r * T;
-        if (x >= G) continue;
-        if (y0 < G) gout[(size_t)y0 * Gs + x] = make_float4(v[0][r].x, v[1][r].x, v[2][r].x, 0.0f);
-        if (y0 + 1 < G) gout[(size_t)(y0 + 1) * Gs + x] = make_float4(v[0][r].y, v[1][r].y, v[2][r].y, 0.0f);
+        for (int r = 0; r < 8; ++r) {
+            const int x = t + r * T;
+            if (x >= G) continue;
+            if (y0 < G) gout[(size_t)y0 * Gs + x] = make_float4(v[0][r].x, v[1][r].x, v[2][r].x, 0.0f);
+            if (y0 + 1 < G) gout[(size_t)(y0 + 1) * Gs + x] = make_float4(v[0][r].y, v[1][r].y, v[2][r].y, 0.0f);
+        }
     }
 }
 
