@@ -237,3 +237,40 @@ def test_split_map_is_the_better_of_the_two_for_the_banks(LOGP):
                         for w0 in range(0, (1 << LOGP) // 2 + 1, 32))
     if LOGP not in (9, 12):
         assert used <= 1.02 * ideal + 6, (used, ideal)
+
+
+def _row_blocks(LOGP):
+    """Rows per block of the forward and inverse row passes (fft_kernels.cu: RegGeom,
+    RowsFwdGeom, RowsInvGeom) and whether the block accesses its output / input columns
+    as 32-byte runs."""
+    T = (1 << LOGP) // 8
+    RG = 1 if T >= 256 else 256 // T
+    seq = T > 512
+    rp = 2 if (not seq and T == 256) else 1
+    RB = RG * (1 if seq else rp)
+    return 2 * RB, (not seq) and RB % 2 == 0
+
+
+@pytest.mark.parametrize("LOGP", range(7, 14))
+def test_row_blocks_cover_the_grid_and_32_byte_runs_stay_aligned_and_inside(LOGP):
+    # every row y < G_max is in some block; the rows a block touches end below ystride
+    # (= G_max rounded up to 32), and where the pass moves 32 bytes per column, each run
+    # starts 32-byte aligned: column base (c NH + kx) ystride and row base ybase + 2q
+    # (q even), in float2 units of 8 bytes, from a 256-byte aligned array
+    P = 1 << LOGP
+    NH = P // 2 + 1
+    rows, wide = _row_blocks(LOGP)
+    for G_max in range(max(1, P // 4 - 40), P // 2 + 1):
+        ystride = -(-G_max // 32) * 32
+        blocks = -(-G_max // rows)
+        assert blocks * rows >= G_max
+        assert (blocks - 1) * rows + rows - 1 < ystride
+        if wide:
+            for blk in (0, 1, blocks - 1):
+                ybase = blk * rows
+                for q in range(0, rows // 2, 2):
+                    for col in (0, 1, 3 * NH - 1):
+                        assert 8 * (col * ystride + ybase + 2 * q) % 32 == 0
+    # the spectrum rows 0..P/2 of the forward pass, into S1 with P rows per column
+    blocks = -(-(P // 2 + 1) // rows)
+    assert (blocks - 1) * rows + rows - 1 < P
