@@ -239,27 +239,39 @@ def test_split_map_is_the_better_of_the_two_for_the_banks(LOGP):
         assert used <= 1.02 * ideal + 6, (used, ideal)
 
 
-def _row_blocks(LOGP):
-    """Rows per block of the forward and inverse row passes (fft_kernels.cu: RegGeom,
-    RowsFwdGeom, RowsInvGeom) and whether the block accesses its output / input columns
-    as 32-byte runs."""
+def _kernel_constant(name):
+    """An integer constexpr of csrc/fft_kernels.cu, read from the source."""
+    import os
+    import re
+    path = os.path.join(os.path.dirname(__file__), "..", "paper_2303_03964_gb300", "csrc", "fft_kernels.cu")
+    with open(path) as f:
+        m = re.search(r"constexpr int %s = (\d+);" % name, f.read())
+    assert m, name
+    return int(m.group(1))
+
+
+def _row_blocks(LOGP, pairs):
+    """Rows per block of a row pass (fft_kernels.cu: RegGeom with RowsFwdGeom or
+    RowsInvGeom, `pairs` row pairs per thread where T = 256) and whether the block
+    accesses its output / input columns as 32-byte runs."""
     T = (1 << LOGP) // 8
     RG = 1 if T >= 256 else 256 // T
     seq = T > 512
-    rp = 2 if (not seq and T == 256) else 1
+    rp = pairs if (not seq and T == 256) else 1
     RB = RG * (1 if seq else rp)
     return 2 * RB, (not seq) and RB % 2 == 0
 
 
 @pytest.mark.parametrize("LOGP", range(7, 14))
-def test_row_blocks_cover_the_grid_and_32_byte_runs_stay_aligned_and_inside(LOGP):
+@pytest.mark.parametrize("which", ["kRowsFwdPairs", "kRowsInvPairs"])
+def test_row_blocks_cover_the_grid_and_32_byte_runs_stay_aligned_and_inside(LOGP, which):
     # every row y < G_max is in some block; the rows a block touches end below ystride
     # (= G_max rounded up to 32), and where the pass moves 32 bytes per column, each run
     # starts 32-byte aligned: column base (c NH + kx) ystride and row base ybase + 2q
     # (q even), in float2 units of 8 bytes, from a 256-byte aligned array
     P = 1 << LOGP
     NH = P // 2 + 1
-    rows, wide = _row_blocks(LOGP)
+    rows, wide = _row_blocks(LOGP, _kernel_constant(which))
     for G_max in range(max(1, P // 4 - 40), P // 2 + 1):
         ystride = -(-G_max // 32) * 32
         blocks = -(-G_max // rows)
